@@ -1,0 +1,205 @@
+"""FP64 CPU oracle for Scheme II (arXiv:1909.02894), loaded through ctypes.
+
+TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg import this package. The product path (the CUDA library and its
+binding) never does. The oracle shares no code with the CUDA path.
+
+``build()`` compiles ``dirac_oracle.c`` with gcc (``-O2 -ffp-contract=off -fopenmp``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+SRC = os.path.join(HERE, "dirac_oracle.c")
+
+CONN_COVARIANT, CONN_PAPER_2D, CONN_NONE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library in place (idempotent)."""
+    if (not force and os.path.exists(LIB_PATH)
+            and os.path.getmtime(LIB_PATH) >= os.path.getmtime(SRC)
+            and os.path.getmtime(LIB_PATH) >= os.path.getmtime(os.path.join(HERE, "dirac_oracle.h"))):
+        return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", tmp, SRC, "-lm"]
+    subprocess.run(cmd, check=True, cwd=HERE)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("ax", C.c_double), ("ay", C.c_double),
+        ("mass", C.c_double), ("c", C.c_double),
+        ("conn", C.c_int),
+        ("pml_wx", C.c_int), ("pml_wy", C.c_int), ("pml_type", C.c_int),
+        ("sigma0", C.c_double), ("theta", C.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER(_Params)
+        dp = C.c_void_p
+        L.oracle_fft.argtypes = [C.c_int, dp, C.c_int]
+        L.oracle_deriv.argtypes = [P, C.c_int, dp, dp]
+        L.oracle_coefficients.argtypes = [P, dp, dp, dp] + [dp] * 8
+        L.oracle_half_step.argtypes = [P, dp, dp, dp, C.c_double, dp]
+        L.oracle_run.argtypes = [P, dp, dp, dp, C.c_double, C.c_long, dp]
+        L.oracle_observables.argtypes = [P, dp, dp, dp, dp, dp, dp]
+        L.oracle_modes_evolve.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double,
+                                          C.c_long, C.c_int, dp, dp, dp, C.c_int, dp, dp, dp]
+        L.oracle_threads.argtypes = []
+        for f in ("oracle_fft", "oracle_deriv", "oracle_coefficients", "oracle_half_step",
+                  "oracle_run", "oracle_observables", "oracle_modes_evolve", "oracle_threads"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a, shape):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.shape == shape, (a.shape, shape)
+    return a
+
+
+@dataclass
+class Problem:
+    """The run parameters of one simulation, as the oracle reads them."""
+
+    nx: int
+    ny: int
+    ax: float
+    ay: float
+    mass: float = 0.0
+    c: float = 1.0
+    conn: int = CONN_COVARIANT
+    pml_wx: int = 0
+    pml_wy: int = 0
+    pml_type: int = 1
+    sigma0: float = 1.0
+    theta: float = 0.0
+    g00: np.ndarray = None
+    g11: np.ndarray = None
+    g22: np.ndarray = None
+
+    @classmethod
+    def from_workload(cls, w, conn=None):
+        return cls(nx=w.nx, ny=w.ny, ax=w.ax, ay=w.ay, mass=w.mass, c=w.c,
+                   conn=w.conn if conn is None else conn, pml_wx=w.pml_width_x,
+                   pml_wy=w.pml_width_y, pml_type=w.pml_type, sigma0=w.sigma0,
+                   theta=w.theta, g00=w.g00, g11=w.g11, g22=w.g22)
+
+    def _params(self):
+        return _Params(self.nx, self.ny, self.ax, self.ay, self.mass, self.c, self.conn,
+                       self.pml_wx, self.pml_wy, self.pml_type, self.sigma0, self.theta)
+
+    def _g(self):
+        s = (self.ny, self.nx)
+        return _f64(self.g00, s), _f64(self.g11, s), _f64(self.g22, s)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} rejected its arguments (rc={rc})")
+
+
+def fft(x, inverse=False):
+    y = np.ascontiguousarray(x, dtype=np.complex128).copy()
+    _check(lib().oracle_fft(y.size, _ptr(y), int(inverse)), "fft")
+    return y
+
+
+def deriv(prob: Problem, f, axis):
+    f = np.ascontiguousarray(f, dtype=np.complex128)
+    out = np.empty_like(f)
+    p = prob._params()
+    _check(lib().oracle_deriv(C.byref(p), axis, _ptr(f), _ptr(out)), "deriv")
+    return out
+
+
+def coefficients(prob: Problem):
+    n = (prob.ny, prob.nx)
+    out = {k: np.empty(n) for k in ("a1", "a2", "meff", "w", "omx", "omy")}
+    out["b1"] = np.empty(n, dtype=np.complex128)
+    out["b2"] = np.empty(n, dtype=np.complex128)
+    g = prob._g()
+    p = prob._params()
+    _check(lib().oracle_coefficients(
+        C.byref(p), *[_ptr(x) for x in g],
+        *[_ptr(out[k]) for k in ("a1", "a2", "meff", "w", "omx", "omy", "b1", "b2")]),
+        "coefficients")
+    return out
+
+
+def half_step(prob: Problem, dt):
+    u = np.empty((prob.ny, prob.nx, 4), dtype=np.complex128)
+    g = prob._g()
+    p = prob._params()
+    _check(lib().oracle_half_step(C.byref(p), *[_ptr(x) for x in g], dt, _ptr(u)), "half_step")
+    return u.reshape(prob.ny, prob.nx, 2, 2)
+
+
+def run(prob: Problem, psi, dt, n_steps):
+    psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    assert psi.shape == (2, prob.ny, prob.nx)
+    g = prob._g()
+    p = prob._params()
+    _check(lib().oracle_run(C.byref(p), *[_ptr(x) for x in g], dt, int(n_steps), _ptr(psi)),
+           "run")
+    return psi
+
+
+def observables(prob: Problem, psi, with_density=False):
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    obs = np.empty(4)
+    dens = np.empty((prob.ny, prob.nx)) if with_density else None
+    g = prob._g()
+    p = prob._params()
+    _check(lib().oracle_observables(C.byref(p), *[_ptr(x) for x in g], _ptr(psi), _ptr(obs),
+                                    _ptr(dens)), "observables")
+    res = {"norm": obs[0], "norm_gamma": obs[1], "energy": obs[2], "energy_imag": obs[3]}
+    if with_density:
+        res["density"] = dens
+    return res
+
+
+def modes_evolve(prob: Problem, g00, g11, g22, dt, n_steps, modes, ix, iy):
+    """modes = [(qx, qy, (A1, A2))]; returns [len(ix)][2] complex."""
+    qx = np.array([m[0] for m in modes], dtype=np.int32)
+    qy = np.array([m[1] for m in modes], dtype=np.int32)
+    amps = np.array([m[2] for m in modes], dtype=np.complex128).reshape(-1)
+    ix = np.ascontiguousarray(ix, dtype=np.int32)
+    iy = np.ascontiguousarray(iy, dtype=np.int32)
+    out = np.empty((ix.size, 2), dtype=np.complex128)
+    p = prob._params()
+    _check(lib().oracle_modes_evolve(C.byref(p), g00, g11, g22, dt, int(n_steps), len(modes),
+                                     _ptr(qx), _ptr(qy), _ptr(amps), ix.size, _ptr(ix),
+                                     _ptr(iy), _ptr(out)), "modes_evolve")
+    return out
+
+
+def threads() -> int:
+    return lib().oracle_threads()

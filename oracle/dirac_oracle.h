@@ -1,0 +1,84 @@
+/*
+ * FP64 CPU oracle for the direction-split explicit pseudospectral step ("Numerical
+ * Scheme II") of Antoine, Fillion-Gourdeau, Lorin and McLean, "Pseudospectral
+ * computational methods for the time-dependent Dirac equation in static curved
+ * spaces" (arXiv:1909.02894), 2D, two-component spinor.
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark may load this library. The product path never calls it. It shares no
+ * code, header, table or constant with the CUDA path.
+ *
+ * Array conventions: real fields are [ny][nx] doubles, x fastest. A spinor is
+ * [2][ny][nx] double complex (interleaved re, im), component-major.
+ * Every function returns 0 on success and a negative value on invalid arguments.
+ *
+ * Parity status: every function below is pinned by the oracle tests except two
+ * modelling choices, which are checked only by invariants: the covariant spin
+ * connection (conserved weighted norm) and the absorbing-layer profile values
+ * (monotone decay, and no effect where the layer is empty).
+ */
+#ifndef DIRAC_ORACLE_H
+#define DIRAC_ORACLE_H
+
+#include <complex.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORACLE_CONN_COVARIANT = 0, ORACLE_CONN_PAPER_2D = 1, ORACLE_CONN_NONE = 2 };
+
+typedef struct {
+  int nx, ny;          /* powers of two (Sec. 5 needs N even; the radix-2 FFT needs 2^k) */
+  double ax, ay;       /* domain [-ax, ax) x [-ay, ay)                                   */
+  double mass, c;      /* m and the speed of light                                       */
+  int conn;            /* spin-connection reading, ORACLE_CONN_*                         */
+  int pml_wx, pml_wy;  /* absorbing-layer width in grid points per side, 0 = none        */
+  int pml_type;        /* 1..6 = the paper's types I..VI (Sec. 3)                        */
+  double sigma0, theta;
+} oracle_params;
+
+/* Forward DFT psi~_p = sum_k psi_k exp(-2 pi i p k / n), inverse with 1/n (Sec. 5). */
+int oracle_fft(int n, double complex *x, int inverse);
+
+/* Spectral derivative [[d_axis]] of a complex [ny][nx] field (Sec. 5, eq. "trick"). */
+int oracle_deriv(const oracle_params *p, int axis, const double complex *in,
+                 double complex *out);
+
+/* Coefficient fields (each [ny][nx]): a1, a2, meff, w, omega_x, omega_y (real) and
+ * b1 = a1/S1, b2 = a2/S2 (complex; real when theta = 0). NULL g means g = 1. */
+int oracle_coefficients(const oracle_params *p, const double *g00, const double *g11,
+                        const double *g22, double *a1, double *a2, double *meff,
+                        double *w, double *omx, double *omy, double complex *b1,
+                        double complex *b2);
+
+/* Half-step matrix U = exp(-i dt/2 [meff sigma_z + F]) per point as 4 complex entries
+ * [u00, u01, u10, u11] per point: out is [ny][nx][4] double complex. */
+int oracle_half_step(const oracle_params *p, const double *g00, const double *g11,
+                     const double *g22, double dt, double complex *u);
+
+/* n_steps of Scheme II from psi (in place): U, x-substep, y-substep, U per step. */
+int oracle_run(const oracle_params *p, const double *g00, const double *g11,
+               const double *g22, double dt, long n_steps, double complex *psi);
+
+/* obs = {norm, norm_gamma, energy_re, energy_im}; density may be NULL. */
+int oracle_observables(const oracle_params *p, const double *g00, const double *g11,
+                       const double *g22, const double complex *psi, double *obs,
+                       double *density);
+
+/* Constant coefficients (scalar g00, g11, g22, no absorbing layer): each plane wave
+ * is an eigenfunction of every sub-step, so the scheme's result after n_steps is a
+ * per-mode 2x2 matrix power. modes: qx[k], qy[k] FFT indices and amps[2k], amps[2k+1]
+ * the two components; evaluated at grid points (ix[s], iy[s]) into out[2s], out[2s+1]. */
+int oracle_modes_evolve(const oracle_params *p, double g00, double g11, double g22,
+                        double dt, long n_steps, int n_modes, const int *qx,
+                        const int *qy, const double complex *amps, int n_pts,
+                        const int *ix, const int *iy, double complex *out);
+
+/* Number of OpenMP threads the oracle uses (1 without OpenMP). */
+int oracle_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,463 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each pin is computed without the oracle's own arithmetic: library routines (numpy FFT,
+scipy expm), closed forms printed in the paper (App. B), exact special cases (constant
+coefficients, the free Dirac propagator), brute-force dense matrices on tiny grids,
+and invariants proved in the paper (Prop. 5.2, Prop. 5.3).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_1909_02894_gb300 import workloads as W
+
+SX = np.array([[0, 1], [1, 0]], dtype=complex)
+SY = np.array([[0, -1j], [1j, 0]], dtype=complex)
+SZ = np.array([[1, 0], [0, -1]], dtype=complex)
+I2 = np.eye(2, dtype=complex)
+
+
+def xi_vec(n, a):
+    q = np.arange(n)
+    p = np.where(q < n // 2, q, q - n)
+    return p * np.pi / a
+
+
+def np_deriv(f, axis, a):
+    """Spectral derivative via numpy's FFT (library routine)."""
+    n = f.shape[1 - axis] if f.ndim == 2 else f.shape[0]
+    xi = xi_vec(n, a)
+    if f.ndim == 1:
+        return np.fft.ifft(1j * xi * np.fft.fft(f))
+    ax = 1 if axis == 0 else 0
+    shape = [1, 1]
+    shape[ax] = n
+    return np.fft.ifft(1j * xi.reshape(shape) * np.fft.fft(f, axis=ax), axis=ax)
+
+
+def problem(oracle, nx, ny, ax, ay, **kw):
+    return oracle.Problem(nx=nx, ny=ny, ax=ax, ay=ay, **kw)
+
+
+# --------------------------------------------------------------------------- T1
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 64])
+def test_t1_fft_matches_brute_force_dft(oracle_lib, n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    k = np.arange(n)
+    Fm = np.exp(-2j * np.pi * np.outer(k, k) / n)  # Sec. 5 DFT, brute force O(N^2)
+    ref = Fm @ x
+    got = oracle_lib.fft(x)
+    assert np.abs(got - ref).max() <= 1e-13 * max(1.0, np.abs(ref).max())
+    inv = oracle_lib.fft(ref, inverse=True)
+    assert np.abs(inv - x).max() <= 1e-13 * max(1.0, np.abs(x).max())
+    assert np.allclose(got, np.fft.fft(x), rtol=0, atol=1e-12)
+
+
+def test_t1_fft_rejects_non_power_of_two(oracle_lib):
+    with pytest.raises(ValueError):
+        oracle_lib.fft(np.ones(6, dtype=complex))
+
+
+# --------------------------------------------------------------------------- T2
+@pytest.mark.parametrize("n,a", [(16, 5.0), (32, 20.0), (64, 3.0)])
+def test_t2_derivative_exact_on_trig_polynomials(oracle_lib, n, a):
+    prob = problem(oracle_lib, n, 8, a, 1.0)
+    x = W.grid_1d(n, a)
+    f = np.zeros((8, n), dtype=complex)
+    df = np.zeros((8, n), dtype=complex)
+    for p in range(1, n // 2):
+        k = p * np.pi / a
+        f += np.sin(k * x) / p + 1j * np.cos(k * x) / (p + 1)
+        df += k * np.cos(k * x) / p - 1j * k * np.sin(k * x) / (p + 1)
+    got = oracle_lib.deriv(prob, f, 0)
+    assert np.abs(got - df).max() <= 1e-12 * np.abs(df).max()
+    # along y with the transposed field
+    prob_y = problem(oracle_lib, 8, n, 1.0, a)
+    got_y = oracle_lib.deriv(prob_y, f.T.copy(), 1)
+    assert np.abs(got_y - df.T).max() <= 1e-12 * np.abs(df).max()
+
+
+@pytest.mark.parametrize("n", [8, 16])
+def test_t2_differentiation_matrix_matches_appendix_b(oracle_lib, n):
+    """App. B: A_kk' = (1/N) sum_p i xi_p exp(i xi_p (x_k - x_k')) (eq. spectral_rep),
+    brute force; and its summed closed form (eq. spectral_rep_final), diagonal by its
+    limit -i pi/(2a). As printed the closed form carries an extra leading factor i;
+    the defining sum fixes the reading pi/(N a) [ ... ] without it."""
+    a = 2.5
+    prob = problem(oracle_lib, n, 2, a, 1.0)
+    A = np.zeros((n, n), dtype=complex)
+    for kp in range(n):
+        e = np.zeros((2, n), dtype=complex)
+        e[:, kp] = 1.0
+        A[:, kp] = oracle_lib.deriv(prob, e, 0)[0]
+    x = W.grid_1d(n, a)
+    xs = xi_vec(n, a)
+    brute = np.array([[np.sum(1j * xs * np.exp(1j * xs * (x[k] - x[kp]))) / n
+                       for kp in range(n)] for k in range(n)])
+    assert np.abs(A - brute).max() <= 1e-13 * np.abs(brute).max()
+    closed = np.zeros((n, n), dtype=complex)
+    for k in range(n):
+        for kp in range(n):
+            if k == kp:
+                closed[k, kp] = -1j * np.pi / (2 * a)
+                continue
+            B = np.pi / a * (x[k] - x[kp])
+            E = np.exp(1j * B)
+            closed[k, kp] = np.pi / (n * a) * (
+                2 * E * np.sin(n * B / 2) / (E - 1) ** 2 + 1j * n * np.cos(n * B / 2) / (E - 1))
+    assert np.abs(A - closed).max() <= 1e-12 * np.abs(closed).max()
+    # skew-Hermitian up to the Nyquist diagonal term (Prop. 5.1's argument)
+    off = A - np.diag(np.diag(A))
+    assert np.abs(off + off.conj().T).max() <= 1e-12
+
+
+# --------------------------------------------------------------------------- T3
+@pytest.mark.parametrize("dt,mass", [(0.3, 0.7), (0.05, 0.0), (1e-6, 0.2), (2.0, 3.0)])
+def test_t3_half_step_matrix_matches_expm(oracle_lib, dt, mass):
+    rng = np.random.default_rng(3)
+    n = 16
+    X, Y = W.mesh(n, n, 4.0, 4.0)
+    g00 = 1.0 + 0.3 * np.exp(-(X ** 2 + Y ** 2) / 3)
+    g11 = 1.0 + 0.5 * np.exp(-((X - 1) ** 2 + Y ** 2) / 2)
+    g22 = 1.0 + 0.4 * rng.uniform() * np.exp(-(X ** 2 + (Y + 1) ** 2) / 2)
+    prob = problem(oracle_lib, n, n, 4.0, 4.0, mass=mass, c=1.3, g00=g00, g11=g11, g22=g22)
+    co = oracle_lib.coefficients(prob)
+    U = oracle_lib.half_step(prob, dt)
+    worst = 0.0
+    for j in range(n):
+        for i in range(n):
+            F = -1j * (co["a1"][j, i] * co["omx"][j, i] * SX + co["a2"][j, i] * co["omy"][j, i] * SY)
+            M = -1j * dt / 2 * (co["meff"][j, i] * SZ + F)
+            worst = max(worst, np.abs(U[j, i] - sla.expm(M)).max())
+    assert worst <= 1e-14
+
+
+def test_t3_coefficients_closed_forms(oracle_lib):
+    """a^j = c sqrt(g00/g_jj), meff = m c^2 sqrt(g00), w = sqrt(g11 g22/g00); the
+    covariant connection of a metric with g22 depending on x only is (1/4) d_x ln g22."""
+    n = 32
+    a = 6.0
+    X, Y = W.mesh(n, n, a, a)
+    k = np.pi / a
+    g22 = 1.0 + 0.2 * np.sin(k * X)            # band-limited, depends on x only
+    g11 = 1.0 + 0.1 * np.cos(2 * k * Y)        # depends on y only
+    g00 = 1.2 * np.ones((n, n))
+    prob = problem(oracle_lib, n, n, a, a, mass=0.5, c=2.0, g00=g00, g11=g11, g22=g22)
+    co = oracle_lib.coefficients(prob)
+    assert np.allclose(co["a1"], 2.0 * np.sqrt(g00 / g11), rtol=1e-15, atol=0)
+    assert np.allclose(co["a2"], 2.0 * np.sqrt(g00 / g22), rtol=1e-15, atol=0)
+    assert np.allclose(co["meff"], 0.5 * 4.0 * np.sqrt(g00), rtol=1e-15, atol=0)
+    assert np.allclose(co["w"], np.sqrt(g11 * g22 / g00), rtol=1e-15, atol=0)
+    # Omega_x = 1/2 d_x ln(w a1) = 1/4 d_x ln g22 (analytic derivative of ln(1+0.2 sin kx));
+    # ln(1+0.2 sin) is not band-limited, so spectral accuracy at n=32 is ~1e-11.
+    ref_x = 0.25 * (0.2 * k * np.cos(k * X)) / g22
+    assert np.abs(co["omx"] - ref_x).max() <= 1e-10
+    ref_y = 0.25 * (-0.1 * 2 * k * np.sin(2 * k * Y)) / g11
+    assert np.abs(co["omy"] - ref_y).max() <= 1e-10
+    # no absorbing layer: b = a
+    assert np.array_equal(co["b1"].real, co["a1"]) and not co["b1"].imag.any()
+
+
+def test_t3_paper_2d_connection_is_quarter_d_ln_g00(oracle_lib):
+    n = 32
+    a = 5.0
+    X, Y = W.mesh(n, n, a, a)
+    k = np.pi / a
+    g00 = np.exp(2 * 0.1 * np.sin(k * X) * np.cos(k * Y))   # Phi = 0.1 sin cos
+    prob = problem(oracle_lib, n, n, a, a, conn=oracle_lib.CONN_PAPER_2D, g00=g00)
+    co = oracle_lib.coefficients(prob)
+    # 1/2 d_x Phi, with Phi band-limited: exact up to rounding
+    assert np.abs(co["omx"] - 0.5 * 0.1 * k * np.cos(k * X) * np.cos(k * Y)).max() <= 1e-13
+    assert np.abs(co["omy"] + 0.5 * 0.1 * k * np.sin(k * X) * np.sin(k * Y)).max() <= 1e-13
+    prob0 = problem(oracle_lib, n, n, a, a, conn=oracle_lib.CONN_NONE, g00=g00)
+    co0 = oracle_lib.coefficients(prob0)
+    assert not co0["omx"].any() and not co0["omy"].any()
+
+
+# --------------------------------------------------------------------------- T4
+def mode_step_matrix(a1, a2, me, dt, kx, ky):
+    """One step of the scheme on a plane wave, built from scipy's expm."""
+    U = sla.expm(-1j * dt / 2 * me * SZ)
+    Kx = a1 * sla.expm(-1j * dt * kx * SX) + (1 - a1) * I2
+    Ky = a2 * sla.expm(-1j * dt * ky * SY) + (1 - a2) * I2
+    return U @ Ky @ Kx @ U
+
+
+@pytest.mark.parametrize("g,mass,c", [((1.0, 1.0, 1.0), 0.0, 1.0), ((1.3, 0.8, 1.1), 0.7, 1.2)])
+def test_t4_constant_metric_per_mode_closed_form(oracle_lib, g, mass, c):
+    nx, ny, ax, ay = 32, 16, 6.0, 4.0
+    modes = [(1, 0, (1.0, 0.5j)), (3, 14, (0.3 - 0.2j, 0.1)), (31, 5, (0.05, -0.4j)),
+             (16, 8, (0.02, 0.01))]  # includes both Nyquist indices
+    psi0 = W.plane_waves(nx, ny, ax, ay, modes)
+    G = [np.full((ny, nx), v) for v in g]
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=G[0], g11=G[1], g22=G[2])
+    dt, n = 0.03, 200
+    got = oracle_lib.run(prob, psi0, dt, n)
+    a1, a2 = c * np.sqrt(g[0] / g[1]), c * np.sqrt(g[0] / g[2])
+    me = mass * c * c * np.sqrt(g[0])
+    xs, ys = xi_vec(nx, ax), xi_vec(ny, ay)
+    X, Y = W.mesh(nx, ny, ax, ay)
+    ref = np.zeros_like(psi0)
+    for qx, qy, amps in modes:
+        T = mode_step_matrix(a1, a2, me, dt, xs[qx], ys[qy])
+        v = np.linalg.matrix_power(T, n) @ np.array(amps)
+        e = np.exp(1j * xs[qx] * (X + ax) + 1j * ys[qy] * (Y + ay))
+        ref[0] += v[0] * e
+        ref[1] += v[1] * e
+    assert W.rel_l2(got, ref) <= 1e-12
+    # the oracle's own per-mode evaluator agrees with the same closed form
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    pts = oracle_lib.modes_evolve(prob, *g, dt, n, modes, ii.ravel(), jj.ravel())
+    assert np.abs(pts[:, 0] - ref[0].ravel()).max() <= 1e-12
+    assert np.abs(pts[:, 1] - ref[1].ravel()).max() <= 1e-12
+
+
+# --------------------------------------------------------------------------- T5
+def test_t5_first_order_convergence_to_free_propagator(oracle_lib):
+    """Flat space: the exact solution is exp(-i T H(xi)) per mode with
+    H(xi) = sigma.xi + m sigma_z, energies +-sqrt(|xi|^2 + m^2). Scheme II is first
+    order in time (Prop. 5.2): the error halves with dt."""
+    n, a, mass, T = 64, 10.0, 0.5, 1.0
+    psi0 = W.wave_packet(n, n, a, a, 1.5, (1.0, -0.5))
+    psi0[1] = 0.5j * psi0[0]
+    prob = problem(oracle_lib, n, n, a, a, mass=mass)
+    xs = xi_vec(n, a)
+    KX, KY = np.meshgrid(xs, xs, indexing="xy")
+    E = np.sqrt(KX ** 2 + KY ** 2 + mass ** 2)
+    h0 = np.fft.fft2(psi0[0])
+    h1 = np.fft.fft2(psi0[1])
+    cs, sn = np.cos(T * E), np.sin(T * E) / E
+    # exp(-i T H) = cos(TE) I - i sin(TE)/E H
+    r0 = cs * h0 - 1j * sn * (mass * h0 + (KX - 1j * KY) * h1)
+    r1 = cs * h1 - 1j * sn * ((KX + 1j * KY) * h0 - mass * h1)
+    exact = np.stack([np.fft.ifft2(r0), np.fft.ifft2(r1)])
+    errs = []
+    for dt in (0.04, 0.02, 0.01, 0.005):
+        got = oracle_lib.run(prob, psi0, dt, int(round(T / dt)))
+        errs.append(W.rel_l2(got, exact))
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(abs(o - 1.0) <= 0.15 for o in orders), (errs, orders)
+    assert errs[-1] < 0.05
+
+
+# --------------------------------------------------------------------------- T6
+def test_t6_flat_energy_by_parseval(oracle_lib):
+    n, a, mass = 32, 6.0, 0.8
+    psi = W.random_state(n, n, 6) * 0.1 + W.wave_packet(n, n, a, a, 1.2, (1, 1))
+    prob = problem(oracle_lib, n, n, a, a, mass=mass)
+    got = oracle_lib.observables(prob, psi)
+    xs = xi_vec(n, a)
+    KX, KY = np.meshgrid(xs, xs, indexing="xy")
+    h0, h1 = np.fft.fft2(psi[0]), np.fft.fft2(psi[1])
+    Hh0 = mass * h0 + (KX - 1j * KY) * h1
+    Hh1 = (KX + 1j * KY) * h0 - mass * h1
+    hh = (2 * a / n) ** 2
+    e = hh / n ** 2 * np.sum(h0.conj() * Hh0 + h1.conj() * Hh1)
+    assert abs(got["energy"] - e.real) <= 1e-12 * abs(e)
+    assert abs(got["energy_imag"] - e.imag) <= 1e-12 * abs(e)
+    assert abs(got["norm"] - hh * np.sum(np.abs(psi) ** 2)) <= 1e-13 * got["norm"]
+    assert got["norm_gamma"] == pytest.approx(got["norm"], rel=1e-14)
+
+
+# --------------------------------------------------------------------------- T7
+def test_t7_flat_norm_is_conserved(oracle_lib):
+    n, a = 64, 10.0
+    psi0 = W.wave_packet(n, n, a, a, 1.5, (2.0, 1.0))
+    prob = problem(oracle_lib, n, n, a, a, mass=0.6)
+    n0 = oracle_lib.observables(prob, psi0)["norm"]
+    got = oracle_lib.run(prob, psi0, 0.02, 200)
+    assert abs(oracle_lib.observables(prob, got)["norm"] / n0 - 1) <= 1e-13
+
+
+def test_t7_prop53_contractive_for_constant_a(oracle_lib):
+    """Prop. 5.3 with a constant 0 <= a <= 1, no connection term and unitary U:
+    b Xi + (1-b) psi with ||Xi|| = ||psi|| gives ||psi*|| <= ||psi|| every step."""
+    w = W.plain_128(n=64, steps=1)
+    prob = oracle_lib.Problem.from_workload(w, conn=oracle_lib.CONN_NONE)
+    prob.mass = 0.3
+    prob.g11 = np.full((64, 64), 1.3)
+    prob.g22 = np.full((64, 64), 1.1)
+    psi = w.psi0
+    last = oracle_lib.observables(prob, psi)["norm"]
+    for _ in range(40):
+        psi = oracle_lib.run(prob, psi, 0.05, 1)
+        cur = oracle_lib.observables(prob, psi)["norm"]
+        assert cur <= last * (1 + 1e-14)
+        last = cur
+
+
+@pytest.mark.parametrize("pml", [0, 6])
+def test_t7_variable_b_growth_bound(oracle_lib, pml):
+    """With b varying in space the pointwise identity |Xi_k| = |psi_k| used in the
+    proof of Prop. 5.3 does not hold (Xi is only unitary as a whole), and the l2 norm
+    can rise slightly. What does hold for 0 <= b <= 1 is the triangle bound
+    ||b Xi + (1-b) psi|| <= (max b + max(1-b)) ||psi|| per direction."""
+    w = W.plain_128(n=64, steps=1)
+    prob = oracle_lib.Problem.from_workload(w, conn=oracle_lib.CONN_NONE)
+    prob.mass = 0.3
+    prob.pml_wx = prob.pml_wy = pml
+    co = oracle_lib.coefficients(prob)
+    b1, b2 = co["b1"].real, co["b2"].real
+    assert b1.min() >= 0 and b1.max() <= 1 and b2.min() >= 0 and b2.max() <= 1
+    bound = (b1.max() + (1 - b1).max()) * (b2.max() + (1 - b2).max())
+    psi = w.psi0
+    last = oracle_lib.observables(prob, psi)["norm"]
+    rises = 0
+    for _ in range(40):
+        psi = oracle_lib.run(prob, psi, 0.05, 1)
+        cur = oracle_lib.observables(prob, psi)["norm"]
+        assert np.sqrt(cur) <= bound * np.sqrt(last) * (1 + 1e-14)
+        rises += cur > last
+        last = cur
+
+
+def test_t7_weighted_norm_drift_is_first_order(oracle_lib):
+    """Covariant connection, no layer: the weighted norm sum w|psi|^2 is conserved by
+    the continuous equation, so its drift after a fixed time is O(dt); the plain l2
+    norm is not conserved in curved space, and its change tends to a non-zero limit."""
+    n, a = 64, 10.0
+    X, Y = W.mesh(n, n, a, a)
+    g = 1.0 + 0.3 * np.exp(-((X - 1) ** 2 + Y ** 2) / 8.0)
+    psi0 = W.wave_packet(n, n, a, a, 1.5, (1.5, 0.5), x0=(-2.0, 0.0))
+    prob = problem(oracle_lib, n, n, a, a, g11=g, g22=1.0 + 0.5 * (g - 1.0))
+    o0 = oracle_lib.observables(prob, psi0)
+    drifts, changes = [], []
+    for dt in (0.04, 0.02, 0.01):
+        got = oracle_lib.observables(prob, oracle_lib.run(prob, psi0, dt, int(round(2.0 / dt))))
+        drifts.append(abs(got["norm_gamma"] - o0["norm_gamma"]))
+        changes.append(abs(got["norm"] - o0["norm"]))
+    orders = [np.log2(drifts[i] / drifts[i + 1]) for i in range(2)]
+    assert all(0.8 <= o <= 1.3 for o in orders), (drifts, orders)
+    # Richardson extrapolation dt -> 0 of the l2 change stays well away from zero
+    assert 2 * changes[2] - changes[1] > 0.5 * changes[2], changes
+
+
+# --------------------------------------------------------------------------- T8
+def test_t8_spectral_convergence_in_h(oracle_lib):
+    """Fixed domain and dt; grids N = 16..128 against N = 256 at shared points."""
+    ref_w = W.plain_128(n=256, steps=50)
+    prob = oracle_lib.Problem.from_workload(ref_w)
+    ref = oracle_lib.run(prob, ref_w.psi0, ref_w.dt, 50)
+    errs = []
+    for n in (32, 64, 128):
+        w = W.plain_128(n=n, steps=50)
+        got = oracle_lib.run(oracle_lib.Problem.from_workload(w), w.psi0, w.dt, 50)
+        s = 256 // n
+        errs.append(W.rel_l2(got, ref[:, ::s, ::s]))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] / errs[2] > 1e3, errs       # faster than any fixed power
+    assert errs[2] < 1e-9, errs
+
+
+# --------------------------------------------------------------------------- T9
+def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
+    """The whole step as a dense 2N x 2N matrix from explicit DFT matrices, the spin
+    connection from numpy's FFT derivative and U from scipy's expm."""
+    npt = nx * ny
+    a1 = c * np.sqrt(g00 / g11)
+    a2 = c * np.sqrt(g00 / g22)
+    me = mass * c * c * np.sqrt(g00)
+    w = np.sqrt(g11 * g22 / g00)
+    omx = 0.5 * np.real(np_deriv(np.log(w * a1), 0, ax))
+    omy = 0.5 * np.real(np_deriv(np.log(w * a2), 1, ay))
+    Ub = np.zeros((2 * npt, 2 * npt), dtype=complex)
+    for j in range(ny):
+        for i in range(nx):
+            k = j * nx + i
+            F = -1j * (a1[j, i] * omx[j, i] * SX + a2[j, i] * omy[j, i] * SY)
+            u = sla.expm(-1j * dt / 2 * (me[j, i] * SZ + F))
+            for r in range(2):
+                for s in range(2):
+                    Ub[r * npt + k, s * npt + k] = u[r, s]
+
+    def line_op(n, a, sig):
+        kk = np.arange(n)
+        Fm = np.exp(-2j * np.pi * np.outer(kk, kk) / n)
+        Fi = np.conj(Fm) / n
+        xs = xi_vec(n, a)
+        blocks = [[None, None], [None, None]]
+        for r in range(2):
+            for s in range(2):
+                d = np.array([sla.expm(-1j * dt * x * sig)[r, s] for x in xs])
+                blocks[r][s] = Fi @ np.diag(d) @ Fm
+        return blocks
+
+    Bx = line_op(nx, ax, SX)
+    By = line_op(ny, ay, SY)
+    Ix, Iy = np.eye(nx), np.eye(ny)
+    Kx = np.zeros((2 * npt, 2 * npt), dtype=complex)
+    Ky = np.zeros((2 * npt, 2 * npt), dtype=complex)
+    for r in range(2):
+        for s in range(2):
+            Kx[r * npt:(r + 1) * npt, s * npt:(s + 1) * npt] = np.kron(Iy, Bx[r][s])
+            Ky[r * npt:(r + 1) * npt, s * npt:(s + 1) * npt] = np.kron(By[r][s], Ix)
+    b1 = np.tile(a1.ravel(), 2)
+    b2 = np.tile(a2.ravel(), 2)
+    Id = np.eye(2 * npt)
+    Sx = np.diag(b1) @ Kx + np.diag(1 - b1) @ Id
+    Sy = np.diag(b2) @ Ky + np.diag(1 - b2) @ Id
+    return Ub @ Sy @ Sx @ Ub
+
+
+def test_t9_brute_force_dense_step(oracle_lib):
+    nx, ny, ax, ay = 8, 4, 3.0, 2.0
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g00 = 1.0 + 0.2 * np.exp(-(X ** 2 + Y ** 2))
+    g11 = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + Y ** 2))
+    g22 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y - 0.3) ** 2))
+    mass, c, dt = 0.7, 1.1, 0.13
+    M = dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt)
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=g00, g11=g11, g22=g22)
+    npt = nx * ny
+    for e in range(2 * npt):
+        v = np.zeros(2 * npt, dtype=complex)
+        v[e] = 1.0
+        got = oracle_lib.run(prob, v.reshape(2, ny, nx), dt, 1).ravel()
+        assert np.abs(got - M[:, e]).max() <= 1e-13
+
+
+# --------------------------------------------------------------------------- T10
+def test_t10_translation_invariance_in_flat_space(oracle_lib):
+    n, a = 32, 5.0
+    psi0 = W.wave_packet(n, n, a, a, 1.0, (1.0, 2.0)) + 0.01 * W.random_state(n, n, 10)
+    prob = problem(oracle_lib, n, n, a, a, mass=0.4)
+    base = oracle_lib.run(prob, psi0, 0.05, 20)
+    shifted = oracle_lib.run(prob, np.roll(psi0, (3, -5), axis=(1, 2)), 0.05, 20)
+    assert np.abs(shifted - np.roll(base, (3, -5), axis=(1, 2))).max() <= 1e-13
+
+
+# ----------------------------------------------------------- absorbing layer
+def test_pml_layer_leaves_the_interior_alone(oracle_lib):
+    """b = a/S differs from a only in the outer `width` points of each axis, and a
+    packet far from the layer evolves the same with and without it."""
+    w = W.plain_128(n=64, steps=10)
+    p0 = oracle_lib.Problem.from_workload(w)
+    p1 = oracle_lib.Problem.from_workload(w)
+    p1.pml_wx, p1.pml_wy = 6, 4
+    c0, c1 = oracle_lib.coefficients(p0), oracle_lib.coefficients(p1)
+    diff_cols = np.nonzero(np.any(c0["b1"] != c1["b1"], axis=0))[0]
+    assert set(diff_cols) == set(range(0, 6)) | set(range(64 - 5, 64))
+    diff_rows = np.nonzero(np.any(c0["b2"] != c1["b2"], axis=1))[0]
+    assert set(diff_rows) == set(range(0, 4)) | set(range(64 - 3, 64))
+    assert np.all(np.abs(c1["b1"]) <= np.abs(c0["b1"]))
+    r0 = oracle_lib.run(p0, w.psi0, w.dt, 10)
+    r1 = oracle_lib.run(p1, w.psi0, w.dt, 10)
+    # the spectral propagator's sinc tails reach the layer at the 1e-5 level, so the
+    # two runs differ slightly, but only slightly
+    assert W.rel_l2(r1, r0) <= 1e-7
+
+
+@pytest.mark.parametrize("ptype", [1, 2, 3, 4, 5, 6])
+def test_pml_types_absorb(oracle_lib, ptype):
+    """A packet sent into the layer loses norm; singular types give b = 0 at |x| = L."""
+    n, a = 64, 8.0
+    psi0 = W.wave_packet(n, n, a, a, 1.0, (3.0, 0.0), x0=(4.0, 0.0))
+    pn = problem(oracle_lib, n, n, a, a)
+    pp = problem(oracle_lib, n, n, a, a, pml_wx=8, pml_wy=8, pml_type=ptype, sigma0=1.0)
+    co = oracle_lib.coefficients(pp)
+    if ptype >= 3:
+        assert co["b1"][0, 0] == 0 and co["b2"][0, 0] == 0
+    n0 = oracle_lib.observables(pn, oracle_lib.run(pn, psi0, 0.05, 80))["norm"]
+    n1 = oracle_lib.observables(pp, oracle_lib.run(pp, psi0, 0.05, 80))["norm"]
+    assert n1 < 0.9 * n0
