@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of the Scheme II step (arXiv:1909.02894) on the GPU.
+
+A bench step is one time step of the whole hot path (half-step U, x pass, y pass,
+half-step U; consecutive U's merged) on the 4096^2 complex64 grid (m=0.5, 16 random
+strain bumps, absorbing layer 128, dt=0.05), whose state and coefficient fields are
+larger than L2, so no flush is needed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--workload large-4096|graphene-1024-c64|graphene-1024-c128|plain-128-c128]
+
+Prints one JSON line. The path does not shard: with N > 1 each rank runs an
+independent replica and `value` sums the ranks ("replicas only", weak scaling).
+The reference arm times the FP64 CPU oracle on the host cores on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1909_02894_gb300 import workloads as W  # noqa: E402
+
+METRIC = "grid-point*steps/s"
+UNIT = "grid-point*steps/s"
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 2 ** 20
+
+
+def workload(name):
+    """(Workload, precision name, algorithmic bytes per grid point per step)."""
+    if name == "large-4096":
+        return W.large_4096(), "c64", 88
+    if name == "graphene-1024-c64":
+        return W.graphene_strained(n=1024), "c64", 88
+    if name == "graphene-1024-c128":
+        return W.graphene_strained(n=1024), "c128", 176
+    if name == "plain-128-c128":
+        return W.plain_128(), "c128", 176
+    raise SystemExit(f"unknown workload {name}")
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d and isinstance(d[k], (int, float)):
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("line_pass.cuh", "launch_impl.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1909_02894_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_name):
+    """DRAM bytes per launch of the line pass from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "line_pass_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_hash") != kernel_hash() or kv.get("workload") != workload_name:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, wl_name):
+    """The FP64 CPU oracle, as it stands, timed on the host cores on a bounded sample."""
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    w, prec, _ = workload(wl_name)
+    prob = oracle.Problem.from_workload(w)
+    pts = w.nx * w.ny
+    # per-step cost from the difference of a 2-step and a 1-step run (setup cancels)
+    t0 = time.perf_counter()
+    oracle.run(prob, w.psi0, w.dt, 1)
+    t1 = time.perf_counter()
+    oracle.run(prob, w.psi0, w.dt, 2)
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9)
+    # One timed step is one oracle time step on the full grid (a K-step run would take
+    # K times several seconds); it is measured as the difference of a 2-step and a
+    # 1-step run so that the coefficient setup cancels.
+    steps = 1
+    value = pts / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "precision": "c128 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                         "sample": f"1 and 2 full oracle steps of {w.name}, difference"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(w):
+    """Oracle timing on a bounded sample of the same workload (about 10-30 s of CPU)."""
+    import oracle
+
+    oracle.build()
+    prob = oracle.Problem.from_workload(w)
+    t0 = time.perf_counter()
+    oracle.run(prob, w.psi0, w.dt, 1)
+    t1 = time.perf_counter()
+    oracle.run(prob, w.psi0, w.dt, 2)
+    t2 = time.perf_counter()
+    per_step = max((t2 - t1) - (t1 - t0), 1e-9)
+    return {"value": w.nx * w.ny / per_step, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"difference of 2-step and 1-step FP64 oracle runs on {w.name}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="large-4096")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-solves", type=int, default=3)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args, args.workload)
+
+    import torch
+
+    import paper_1909_02894_gb300 as D
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w, prec_name, bytes_pt = workload(args.workload)
+    prec = D.DIRAC_C64 if prec_name == "c64" else D.DIRAC_C128
+    stream = torch.cuda.current_stream()
+    sim = D.Simulation(w, precision=prec, stream=stream.cuda_stream)
+    sim.set_state(w.psi0)
+    pts = w.nx * w.ny
+    warm = max(3, args.warmup)
+    sim.step(warm, w.dt)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region
+    l0 = D.dirac_launch_count(sim.ctx)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        ev0.record(stream)
+        sim.step(args.steps, w.dt)
+        ev1.record(stream)
+        barrier()
+    launches = D.dirac_launch_count(sim.ctx) - l0
+    ms = ev0.elapsed_time(ev1)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = pts * args.steps * world / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (the fused line pass, 2 launches per step;
+    # the timed region holds nothing else, so its average launch duration is ms/launches)
+    peak, peak_kind = hbm_peak()
+    per_launch_s = ms * 1e-3 / max(1, launches)
+    alg_bytes_launch = bytes_pt * pts / 2.0
+    achieved = alg_bytes_launch / per_launch_s / 1e9
+    traffic = ncu_traffic(args.workload)
+
+    # ---- end to end through the public API with pinned host buffers
+    e2e = None
+    if args.e2e_solves > 0:
+        host_in = torch.empty((2, w.ny, w.nx), dtype=torch.complex128, pin_memory=True)
+        host_in.numpy()[...] = w.psi0
+        host_out = torch.empty_like(host_in).pin_memory()
+        solve_steps = min(args.steps, w.steps)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_solves):
+            D.lib().dirac_set_state(sim.ctx, host_in.data_ptr(), 0)
+            sim.step(solve_steps, w.dt)
+            D.lib().dirac_get_state(sim.ctx, host_out.data_ptr(), 0)
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": pts * solve_steps * args.e2e_solves * world / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": host_in.numel() * 16,
+               "d2h_bytes_per_step": host_out.numel() * 16,
+               "step": f"one solve: set_state(host) + {solve_steps} steps + get_state(host)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == D.DIRAC_C64 else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "precision": prec_name, "grid": [w.nx, w.ny],
+                       "dt": w.dt, "absorber": w.pml_width_x, "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (no flush)"
+                       if bytes_pt * pts > L2_BYTES else "working set fits L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind, "kernel": "line_pass_kernel",
+                         "algorithmic_bytes_per_point_step": bytes_pt},
+            "clocks": clk.summary(),
+            "gpu_launches": int(launches),
+            "e2e": e2e,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w)
+        print(json.dumps(line))
+    sim.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

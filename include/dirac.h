@@ -1,0 +1,148 @@
+/*
+ * dirac.h -- C ABI of the GB300 (sm_103a) implementation of the direction-split explicit
+ * pseudospectral step ("Numerical Scheme II", Sec. 5.2) for the 2D time-dependent Dirac
+ * equation in a static curved space, from Antoine, Fillion-Gourdeau, Lorin, McLean,
+ * "Pseudospectral computational methods for the time-dependent Dirac equation in static
+ * curved spaces" (arXiv:1909.02894).
+ *
+ * The problem (Sec. 2.2, Sec. 5, Sec. 6 for the 2D two-component form):
+ *   i d_t psi = H psi,  H = -i sum_{j=x,y} a^j(x) sigma_j (d_j + Omega_j(x)) + meff(x) sigma_z
+ * on the periodic grid x_k = -a + k h, h = 2a/N (Sec. 5), with a diagonal static metric
+ * ds^2 = g00 dt^2 - g11 dx^2 - g22 dy^2 giving a^j = c sqrt(g00/g_jj),
+ * meff = m c^2 sqrt(g00), and absorbing layers that replace a^j by b^j = a^j / S^j(x^j)
+ * (Sec. 3, and Sec. 5.2 "replacing a^i by a^i/S^i").
+ *
+ * One time step dt (Sec. 4.2 eq. op_split_curved with Sec. 5.2 eq. poly_mod and
+ * second_scheme):
+ *   S1  psi <- U psi,  U = exp(-i dt/2 [meff sigma_z + F]),  F = -i sum_j a^j Omega_j sigma_j
+ *   S2  rows:    Xi = F_x^-1[exp(-i dt xi sigma_x) F_x psi],  psi <- b^1 Xi + (1 - b^1) psi
+ *   S3  columns: Xi = F_y^-1[exp(-i dt xi sigma_y) F_y psi],  psi <- b^2 Xi + (1 - b^2) psi
+ *   S4  psi <- U psi
+ *
+ * Conventions shared by every call:
+ *   - Real fields are [ny][nx] doubles, x fastest (the paper's vector ordering, App. C).
+ *   - A spinor crossing the ABI is [2][ny][nx] complex128 (interleaved re, im), component
+ *     major, in both precisions; DIRAC_C64 contexts convert on the device.
+ *   - The caller owns every array it passes; create/set_state copy what they need, so the
+ *     caller may free its arrays when the call returns. The context owns all of its device
+ *     memory until dirac_destroy.
+ *   - Every call returns a dirac_status; no exception or exit crosses the ABI.
+ *     dirac_last_error() gives the detail of the last failure on a context.
+ *   - Calls on one context are not thread-safe; distinct contexts are independent.
+ */
+#ifndef DIRAC_H
+#define DIRAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dirac_ctx dirac_ctx;
+typedef struct dirac_batch dirac_batch;
+
+typedef enum {
+  DIRAC_OK = 0,
+  DIRAC_EINVAL = 1,       /* invalid argument (sizes, pointers, non-positive g, dt <= 0) */
+  DIRAC_ENOMEM = 2,       /* device or host allocation failed                           */
+  DIRAC_EUNSUPPORTED = 3, /* valid but outside this build (e.g. theta != 0)              */
+  DIRAC_ECUDA = 4,        /* a CUDA runtime call failed                                   */
+  DIRAC_ETIMEOUT = 5,     /* a bounded device wait ran out                                */
+  DIRAC_ENONFINITE = 6,   /* the state holds NaN or Inf                                   */
+  DIRAC_ESTATE = 7        /* call out of order (e.g. step before set_state)               */
+} dirac_status;
+
+typedef enum { DIRAC_C64 = 0, DIRAC_C128 = 1 } dirac_precision;
+
+/* Spin connection Omega_j (Sec. 2.2). COVARIANT: Omega_j = 1/2 d_j ln(w a^j) with
+ * w = sqrt(g11 g22 / g00) (= sqrt|g| g^00, the weight of the conserved norm, eq. l2gamma).
+ * PAPER_2D: Omega_j = 1/2 d_j Phi with g00 = exp(2 Phi), as printed for Experiment 3.
+ * NONE: Omega_j = 0. d_j is the spectral derivative of the sampled field (eq. trick),
+ * real part. */
+typedef enum { DIRAC_CONN_COVARIANT = 0, DIRAC_CONN_PAPER_2D = 1, DIRAC_CONN_NONE = 2 } dirac_connection;
+
+/* Grid sizes: powers of two, 16 <= nx, ny <= 4096 (Sec. 5 needs N even). */
+typedef struct { int nx, ny; } dirac_grid;
+
+/* Domain [-ax, ax) x [-ay, ay), ax, ay > 0 (Sec. 5). */
+typedef struct { double ax, ay; } dirac_domain;
+
+/* Diagonal static metric (eq. alpha_form needs alpha^j = a^j(x) alpha^j). Host arrays
+ * [ny][nx], entries > 0; a NULL pointer means the constant 1. g12 = 0. */
+typedef struct {
+  const double *g00, *g11, *g22;
+  dirac_connection conn;
+} dirac_metric;
+
+/* Absorbing layer (Sec. 3): width_x/width_y grid points per side (0 = none, < N/2),
+ * type 1..6 = the paper's profiles I..VI, sigma0 = Sigma_0, theta = stretching angle.
+ * theta != 0 makes b complex and returns DIRAC_EUNSUPPORTED in this build. */
+typedef struct {
+  int width_x, width_y;
+  int type;
+  double sigma0, theta;
+} dirac_absorber;
+
+/* Observables (Sec. 2.2 eq. l2gamma, Prop. 5.3's discrete l2 norm, Sec. 6.2 density):
+ *   norm       = hx hy sum |psi|^2
+ *   norm_gamma = hx hy sum w |psi|^2
+ *   energy     = hx hy sum w Re(psi^dagger H psi), energy_imag its imaginary part,
+ *                with H as above without absorbing layers.
+ * All reductions are accumulated in FP64. */
+typedef struct {
+  double norm, norm_gamma, energy, energy_imag;
+} dirac_obs;
+
+/* Creates a context: validates the arguments, copies the metric to the device and
+ * precomputes a^j, meff, w, Omega_j, b^j and the layer profile in FP64 on the GPU.
+ * metric may be NULL (flat space), absorber may be NULL (no layer). c > 0, mass real.
+ * cuda_stream: a cudaStream_t to launch on, or NULL for a stream the context creates.
+ * On success *out holds the context; on failure *out is NULL. */
+dirac_status dirac_create(const dirac_grid *grid, const dirac_domain *domain,
+                          const dirac_metric *metric, double mass, double c,
+                          const dirac_absorber *absorber, dirac_precision precision,
+                          void *cuda_stream, dirac_ctx **out);
+
+/* Sets the state from psi, [2][ny][nx] complex128. on_device = 0: psi is host memory,
+ * copied before return; on_device = 1: psi is device memory, read on the context's
+ * stream (the caller keeps it alive until the stream reaches this point). */
+dirac_status dirac_set_state(dirac_ctx *ctx, const double *psi, int on_device);
+
+/* Writes the state to psi_out, [2][ny][nx] complex128, host (on_device = 0, returns when
+ * the copy is done) or device (on_device = 1, enqueued on the context's stream). */
+dirac_status dirac_get_state(dirac_ctx *ctx, double *psi_out, int on_device);
+
+/* Advances the state by n_steps steps of size dt (n_steps >= 0, dt > 0), enqueued on the
+ * context's stream without host synchronisation. Consecutive steps merge the trailing
+ * U of one step with the leading U of the next (U U, the same matrix in closed form).
+ * A new dt recomputes U and the k-space phase tables in FP64 first. */
+dirac_status dirac_step(dirac_ctx *ctx, long n_steps, double dt);
+
+/* Computes the observables (synchronises the stream). density_or_NULL, if not NULL, is a
+ * host [ny][nx] array that receives |psi_1|^2 + |psi_2|^2. Returns DIRAC_ENONFINITE
+ * (after filling *out) if the norm is not finite. */
+dirac_status dirac_observables(dirac_ctx *ctx, dirac_obs *out, double *density_or_NULL);
+
+/* Blocks until all work enqueued on the context's stream has finished. */
+dirac_status dirac_synchronize(dirac_ctx *ctx);
+
+/* Text of the last error on ctx (or of the last failed dirac_create when ctx is NULL).
+ * The string stays valid until the next call on the same context. */
+const char *dirac_last_error(const dirac_ctx *ctx);
+
+/* Releases the context and all its device memory. NULL is allowed. */
+void dirac_destroy(dirac_ctx *ctx);
+
+/* Launch parameters of the two fused passes (each pass: FFT along a line, k-space
+ * multiply, inverse FFT, combine, transposed store). threads: threads per CTA for that
+ * line length; 0 = the built-in default. Used by the autotuner. */
+dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_pass);
+
+/* Number of kernel launches this context has enqueued so far (for accounting). */
+long dirac_launch_count(const dirac_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

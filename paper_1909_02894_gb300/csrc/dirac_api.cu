@@ -1,0 +1,479 @@
+// C ABI of the Scheme II library: context management and the host side of each call.
+// Every numerical step runs in the kernels of this library; the host only validates,
+// allocates, enqueues and copies.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dirac.h"
+#include "internal.h"
+
+using namespace dgb;
+
+struct dirac_ctx {
+  int nx = 0, ny = 0;
+  double ax = 0, ay = 0, mass = 0, c = 1;
+  dirac_precision prec = DIRAC_C64;
+  int conn = 0;
+  dirac_absorber abs = {0, 0, 1, 1.0, 0.0};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  bool u_identity = false;  // no mass and no connection: U = I exactly
+
+  // FP64 fields in the normal layout [ny][nx]
+  double *a1 = nullptr, *a2 = nullptr, *meff = nullptr, *w = nullptr, *omx = nullptr,
+         *omy = nullptr;
+  double *sxinv = nullptr, *syinv = nullptr;
+  // state and per-pass coefficients in the state precision
+  void *psi = nullptr, *psiT = nullptr;
+  void *beta1 = nullptr, *beta2T = nullptr;
+  void *u_n = nullptr, *u_t = nullptr, *u2_t = nullptr;
+  void *tw_x = nullptr, *tw_y = nullptr, *mult_x = nullptr, *mult_y = nullptr,
+       *dmult_x = nullptr, *dmult_y = nullptr;
+  double* staging = nullptr;  // [2][ny][nx] complex128 for host transfers
+  void *scratch1 = nullptr, *scratch2 = nullptr;
+  double *partials = nullptr, *result = nullptr, *density = nullptr;
+
+  double dt_cached = 0.0;
+  bool state_set = false;
+  int threads_x = 0, threads_y = 0;
+  long launches = 0;
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+static thread_local std::string g_create_error;
+
+static size_t npts(const dirac_ctx* c) { return (size_t)c->nx * c->ny; }
+
+static dirac_status fail(dirac_ctx* c, dirac_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+static dirac_status cuda_fail(dirac_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, e == cudaErrorMemoryAllocation ? DIRAC_ENOMEM : DIRAC_ECUDA, m);
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+static cudaError_t dalloc(dirac_ctx* ctx, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) ctx->allocs.push_back(*p);
+  return e;
+}
+
+static void free_all(dirac_ctx* ctx) {
+  for (void* p : ctx->allocs) cudaFree(p);
+  ctx->allocs.clear();
+}
+
+// ------------------------------------------------------------------ precision dispatch
+template <typename T>
+static LinePassArgs<T> pass_args(dirac_ctx* ctx, int axis) {
+  LinePassArgs<T> a{};
+  a.L = axis == 0 ? ctx->nx : ctx->ny;
+  a.n_lines = axis == 0 ? ctx->ny : ctx->nx;
+  a.sigma = axis;
+  a.tw = (const Cx<T>*)(axis == 0 ? ctx->tw_x : ctx->tw_y);
+  return a;
+}
+
+template <typename T>
+static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
+  cudaStream_t st = ctx->stream;
+  if (!ctx->u_identity) {
+    CK(launch_halfstep<T>(ctx->a1, ctx->a2, ctx->meff, ctx->omx, ctx->omy, ctx->nx, ctx->ny, dt,
+                          (Q4<T>*)ctx->u_n, (Q4<T>*)ctx->u_t, (Q4<T>*)ctx->u2_t, st),
+       "half-step matrices");
+    ctx->launches += 1;
+  }
+  CK(launch_step_mult<T>(ctx->nx, ctx->ax, dt, (Q4<T>*)ctx->mult_x, st), "x multipliers");
+  CK(launch_step_mult<T>(ctx->ny, ctx->ay, dt, (Q4<T>*)ctx->mult_y, st), "y multipliers");
+  ctx->launches += 2;
+  ctx->dt_cached = dt;
+  return DIRAC_OK;
+}
+
+template <typename T>
+static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
+  if (dt != ctx->dt_cached) {
+    dirac_status s = tables_for_dt<T>(ctx, dt);
+    if (s != DIRAC_OK) return s;
+  }
+  LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
+  ax.in = (const Q4<T>*)ctx->psi;
+  ax.out = (Q4<T>*)ctx->psiT;
+  ax.mult = (const Q4<T>*)ctx->mult_x;
+  ax.beta = (const T*)ctx->beta1;
+  ay.in = (const Q4<T>*)ctx->psiT;
+  ay.out = (Q4<T>*)ctx->psi;
+  ay.mult = (const Q4<T>*)ctx->mult_y;
+  ay.beta = (const T*)ctx->beta2T;
+  for (long s = 0; s < n; ++s) {
+    ax.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
+    ax.u_store = nullptr;
+    CK(launch_line_pass<T>(ax, MODE_STEP, ctx->threads_x, ctx->stream), "x pass");
+    ay.u_load = nullptr;
+    ay.u_store = ctx->u_identity ? nullptr
+                                 : (const Q4<T>*)(s + 1 == n ? ctx->u_t : ctx->u2_t);
+    CK(launch_line_pass<T>(ay, MODE_STEP, ctx->threads_y, ctx->stream), "y pass");
+    ctx->launches += 2;
+  }
+  return DIRAC_OK;
+}
+
+// Spectral derivatives of the state: dx (normal layout) into scratch1, dy into scratch2.
+// Uses psiT as the transposed intermediate.
+template <typename T>
+static dirac_status state_derivatives(dirac_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
+  // y derivative: transpose psi -> scratch1 ([nx][ny]); derivative pass stores it back
+  // transposed, i.e. in the normal layout, into scratch2.
+  CK(launch_transpose<T>((const Q4<T>*)ctx->psi, (Q4<T>*)ctx->scratch1, ctx->ny, ctx->nx, st),
+     "transpose");
+  ay.in = (const Q4<T>*)ctx->scratch1;
+  ay.out = (Q4<T>*)ctx->scratch2;
+  ay.mult = (const Q4<T>*)ctx->dmult_y;
+  CK(launch_line_pass<T>(ay, MODE_DERIV, 0, st), "y derivative");
+  // x derivative: psi -> psiT (transposed), then back to the normal layout in scratch1.
+  ax.in = (const Q4<T>*)ctx->psi;
+  ax.out = (Q4<T>*)ctx->psiT;
+  ax.mult = (const Q4<T>*)ctx->dmult_x;
+  CK(launch_line_pass<T>(ax, MODE_DERIV, 0, st), "x derivative");
+  CK(launch_transpose<T>((const Q4<T>*)ctx->psiT, (Q4<T>*)ctx->scratch1, ctx->nx, ctx->ny, st),
+     "transpose");
+  ctx->launches += 4;
+  return DIRAC_OK;
+}
+
+template <typename T>
+static dirac_status observables_impl(dirac_ctx* ctx, dirac_obs* out, double* density_host) {
+  cudaStream_t st = ctx->stream;
+  const size_t n = npts(ctx);
+  if (!ctx->scratch1) {
+    CK(dalloc(ctx, &ctx->scratch1, n * sizeof(Q4<T>)), "scratch");
+    CK(dalloc(ctx, &ctx->scratch2, n * sizeof(Q4<T>)), "scratch");
+  }
+  dirac_status s = state_derivatives<T>(ctx);
+  if (s != DIRAC_OK) return s;
+  if (density_host && !ctx->density) CK(dalloc(ctx, (void**)&ctx->density, n * sizeof(double)), "density");
+  const int blocks = observables_blocks(n);
+  CK(launch_observables<T>((const Q4<T>*)ctx->psi, (const Q4<T>*)ctx->scratch1,
+                           (const Q4<T>*)ctx->scratch2, ctx->a1, ctx->a2, ctx->meff, ctx->w,
+                           ctx->omx, ctx->omy, n, density_host ? ctx->density : nullptr,
+                           ctx->partials, blocks, st),
+     "observables");
+  const double hxhy = (2.0 * ctx->ax / ctx->nx) * (2.0 * ctx->ay / ctx->ny);
+  CK(launch_reduce_partials(ctx->partials, blocks, hxhy, ctx->result, st), "reduce");
+  ctx->launches += 2;
+  double r[4];
+  CK(cudaMemcpyAsync(r, ctx->result, sizeof(r), cudaMemcpyDeviceToHost, st), "copy result");
+  if (density_host)
+    CK(cudaMemcpyAsync(density_host, ctx->density, n * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "copy density");
+  CK(cudaStreamSynchronize(st), "synchronize");
+  out->norm = r[0];
+  out->norm_gamma = r[1];
+  out->energy = r[2];
+  out->energy_imag = r[3];
+  if (!isfinite(r[0]) || !isfinite(r[1]) || !isfinite(r[2]) || !isfinite(r[3]))
+    return fail(ctx, DIRAC_ENONFINITE, "the state holds non-finite values");
+  return DIRAC_OK;
+}
+
+template <typename T>
+static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
+  cudaStream_t st = ctx->stream;
+  const size_t n = npts(ctx);
+  const int nx = ctx->nx, ny = ctx->ny;
+  // FP64 fields
+  double** f64[] = {&ctx->a1, &ctx->a2, &ctx->meff, &ctx->w, &ctx->omx, &ctx->omy};
+  for (double** p : f64) CK(dalloc(ctx, (void**)p, n * sizeof(double)), "allocate fields");
+  CK(dalloc(ctx, (void**)&ctx->sxinv, nx * sizeof(double)), "allocate layer");
+  CK(dalloc(ctx, (void**)&ctx->syinv, ny * sizeof(double)), "allocate layer");
+  // state, coefficient fields, tables
+  CK(dalloc(ctx, &ctx->psi, n * sizeof(Q4<T>)), "allocate state");
+  CK(dalloc(ctx, &ctx->psiT, n * sizeof(Q4<T>)), "allocate state");
+  CK(dalloc(ctx, &ctx->beta1, n * sizeof(T)), "allocate coefficients");
+  CK(dalloc(ctx, &ctx->beta2T, n * sizeof(T)), "allocate coefficients");
+  if (!ctx->u_identity) {
+    CK(dalloc(ctx, &ctx->u_n, n * sizeof(Q4<T>)), "allocate half-step");
+    CK(dalloc(ctx, &ctx->u_t, n * sizeof(Q4<T>)), "allocate half-step");
+    CK(dalloc(ctx, &ctx->u2_t, n * sizeof(Q4<T>)), "allocate half-step");
+  }
+  CK(dalloc(ctx, &ctx->tw_x, nx * sizeof(Cx<T>)), "allocate tables");
+  CK(dalloc(ctx, &ctx->tw_y, ny * sizeof(Cx<T>)), "allocate tables");
+  CK(dalloc(ctx, &ctx->mult_x, nx * sizeof(Q4<T>)), "allocate tables");
+  CK(dalloc(ctx, &ctx->mult_y, ny * sizeof(Q4<T>)), "allocate tables");
+  CK(dalloc(ctx, &ctx->dmult_x, nx * sizeof(Q4<T>)), "allocate tables");
+  CK(dalloc(ctx, &ctx->dmult_y, ny * sizeof(Q4<T>)), "allocate tables");
+  CK(dalloc(ctx, (void**)&ctx->staging, 2 * n * 2 * sizeof(double)), "allocate staging");
+  CK(dalloc(ctx, (void**)&ctx->partials, 4 * sizeof(double) * observables_blocks(n)), "allocate");
+  CK(dalloc(ctx, (void**)&ctx->result, 4 * sizeof(double)), "allocate");
+
+  // metric upload: the staging buffer holds the three fields during creation
+  double* gdev[3] = {nullptr, nullptr, nullptr};
+  for (int f = 0; f < 3; ++f) {
+    if (g_host[f]) {
+      gdev[f] = ctx->staging + (size_t)f * n;
+      CK(cudaMemcpyAsync(gdev[f], g_host[f], n * sizeof(double), cudaMemcpyHostToDevice, st),
+         "upload metric");
+    }
+  }
+  // The log fields and their derivatives use psi/psiT-sized scratch in FP64.
+  void *logs = nullptr, *logsT = nullptr, *dxT = nullptr, *dy = nullptr;
+  CK(cudaMallocAsync(&logs, n * sizeof(Q4<double>), st), "allocate precompute scratch");
+  CK(cudaMallocAsync(&logsT, n * sizeof(Q4<double>), st), "allocate precompute scratch");
+  CK(cudaMallocAsync(&dxT, n * sizeof(Q4<double>), st), "allocate precompute scratch");
+  CK(cudaMallocAsync(&dy, n * sizeof(Q4<double>), st), "allocate precompute scratch");
+  CK(launch_metric_fields(gdev[0], gdev[1], gdev[2], (int)n, ctx->c, ctx->mass, ctx->conn,
+                          ctx->a1, ctx->a2, ctx->meff, ctx->w, (Q4<double>*)logs, st),
+     "metric fields");
+  ctx->launches += 1;
+  if (ctx->conn == DIRAC_CONN_NONE) {
+    CK(cudaMemsetAsync(ctx->omx, 0, n * sizeof(double), st), "zero connection");
+    CK(cudaMemsetAsync(ctx->omy, 0, n * sizeof(double), st), "zero connection");
+  } else {
+    // FP64 spectral derivatives with the same fused line pass (derivative mode)
+    void *tx = nullptr, *ty = nullptr, *mx = nullptr, *my = nullptr;
+    CK(cudaMallocAsync(&tx, nx * sizeof(Cx<double>), st), "allocate");
+    CK(cudaMallocAsync(&ty, ny * sizeof(Cx<double>), st), "allocate");
+    CK(cudaMallocAsync(&mx, nx * sizeof(Q4<double>), st), "allocate");
+    CK(cudaMallocAsync(&my, ny * sizeof(Q4<double>), st), "allocate");
+    CK(launch_twiddles<double>(nx, (Cx<double>*)tx, st), "twiddles");
+    CK(launch_twiddles<double>(ny, (Cx<double>*)ty, st), "twiddles");
+    CK(launch_deriv_mult<double>(nx, ctx->ax, (Q4<double>*)mx, st), "derivative table");
+    CK(launch_deriv_mult<double>(ny, ctx->ay, (Q4<double>*)my, st), "derivative table");
+    LinePassArgs<double> d{};
+    d.L = nx; d.n_lines = ny; d.sigma = 0; d.tw = (const Cx<double>*)tx;
+    d.mult = (const Q4<double>*)mx; d.in = (const Q4<double>*)logs; d.out = (Q4<double>*)dxT;
+    CK(launch_line_pass<double>(d, MODE_DERIV, 0, st), "x derivative of log fields");
+    CK(launch_transpose<double>((const Q4<double>*)logs, (Q4<double>*)logsT, ny, nx, st),
+       "transpose");
+    d.L = ny; d.n_lines = nx; d.sigma = 1; d.tw = (const Cx<double>*)ty;
+    d.mult = (const Q4<double>*)my; d.in = (const Q4<double>*)logsT; d.out = (Q4<double>*)dy;
+    CK(launch_line_pass<double>(d, MODE_DERIV, 0, st), "y derivative of log fields");
+    const double fac = ctx->conn == DIRAC_CONN_PAPER_2D ? 0.25 : 0.5;
+    CK(launch_omega((const Q4<double>*)dxT, (const Q4<double>*)dy, nx, ny, fac, ctx->omx,
+                    ctx->omy, st),
+       "spin connection");
+    ctx->launches += 8;
+    CK(cudaFreeAsync(tx, st), "free"); CK(cudaFreeAsync(ty, st), "free");
+    CK(cudaFreeAsync(mx, st), "free"); CK(cudaFreeAsync(my, st), "free");
+  }
+  CK(cudaFreeAsync(logs, st), "free"); CK(cudaFreeAsync(logsT, st), "free");
+  CK(cudaFreeAsync(dxT, st), "free"); CK(cudaFreeAsync(dy, st), "free");
+  // absorbing layer and b - 1
+  CK(launch_pml(nx, ctx->ax, ctx->abs.width_x, ctx->abs.type, ctx->abs.sigma0, ctx->sxinv, st),
+     "layer x");
+  CK(launch_pml(ny, ctx->ay, ctx->abs.width_y, ctx->abs.type, ctx->abs.sigma0, ctx->syinv, st),
+     "layer y");
+  CK(launch_beta<T>(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, nx, ny, (T*)ctx->beta1,
+                    (T*)ctx->beta2T, st),
+     "b - 1");
+  CK(launch_twiddles<T>(nx, (Cx<T>*)ctx->tw_x, st), "twiddles");
+  CK(launch_twiddles<T>(ny, (Cx<T>*)ctx->tw_y, st), "twiddles");
+  CK(launch_deriv_mult<T>(nx, ctx->ax, (Q4<T>*)ctx->dmult_x, st), "derivative table");
+  CK(launch_deriv_mult<T>(ny, ctx->ay, (Q4<T>*)ctx->dmult_y, st), "derivative table");
+  ctx->launches += 7;
+  CK(cudaStreamSynchronize(st), "create");
+  ctx->dt_cached = 0.0;
+  return DIRAC_OK;
+}
+
+// ------------------------------------------------------------------------ the ABI
+extern "C" {
+
+dirac_status dirac_create(const dirac_grid* grid, const dirac_domain* domain,
+                          const dirac_metric* metric, double mass, double c,
+                          const dirac_absorber* absorber, dirac_precision precision,
+                          void* cuda_stream, dirac_ctx** out) {
+  if (!out) return fail(nullptr, DIRAC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!grid || !domain) return fail(nullptr, DIRAC_EINVAL, "grid and domain are required");
+  if (!pow2_in(grid->nx, 16, 4096) || !pow2_in(grid->ny, 16, 4096))
+    return fail(nullptr, DIRAC_EINVAL, "nx and ny must be powers of two in [16, 4096]");
+  if (!(domain->ax > 0.0) || !(domain->ay > 0.0) || !isfinite(domain->ax) || !isfinite(domain->ay))
+    return fail(nullptr, DIRAC_EINVAL, "domain half-widths must be positive and finite");
+  if (!(c > 0.0) || !isfinite(c) || !isfinite(mass))
+    return fail(nullptr, DIRAC_EINVAL, "c must be positive and mass finite");
+  if (precision != DIRAC_C64 && precision != DIRAC_C128)
+    return fail(nullptr, DIRAC_EINVAL, "unknown precision");
+  dirac_absorber ab = {0, 0, 1, 1.0, 0.0};
+  if (absorber) {
+    ab = *absorber;
+    if (ab.width_x < 0 || ab.width_y < 0 || ab.width_x >= grid->nx / 2 ||
+        ab.width_y >= grid->ny / 2)
+      return fail(nullptr, DIRAC_EINVAL, "absorber widths must be in [0, N/2)");
+    if ((ab.width_x > 0 || ab.width_y > 0) && (ab.type < 1 || ab.type > 6))
+      return fail(nullptr, DIRAC_EINVAL, "absorber type must be 1..6");
+    if (!isfinite(ab.sigma0) || ab.sigma0 < 0.0 || !isfinite(ab.theta))
+      return fail(nullptr, DIRAC_EINVAL, "absorber sigma0 must be >= 0 and theta finite");
+    if (ab.theta != 0.0 && (ab.width_x > 0 || ab.width_y > 0))
+      return fail(nullptr, DIRAC_EUNSUPPORTED, "complex stretching (theta != 0) is not built");
+  }
+  int conn = DIRAC_CONN_COVARIANT;
+  const double* g_host[3] = {nullptr, nullptr, nullptr};
+  if (metric) {
+    conn = metric->conn;
+    if (conn < 0 || conn > 2) return fail(nullptr, DIRAC_EINVAL, "unknown connection mode");
+    g_host[0] = metric->g00;
+    g_host[1] = metric->g11;
+    g_host[2] = metric->g22;
+    const size_t n = (size_t)grid->nx * grid->ny;
+    for (int f = 0; f < 3; ++f) {
+      if (!g_host[f]) continue;
+      for (size_t k = 0; k < n; ++k) {
+        const double v = g_host[f][k];
+        if (!(v > 0.0) || !isfinite(v))
+          return fail(nullptr, DIRAC_EINVAL, "metric entries must be positive and finite");
+      }
+    }
+  }
+  dirac_ctx* ctx = new (std::nothrow) dirac_ctx();
+  if (!ctx) return fail(nullptr, DIRAC_ENOMEM, "host allocation failed");
+  ctx->nx = grid->nx;
+  ctx->ny = grid->ny;
+  ctx->ax = domain->ax;
+  ctx->ay = domain->ay;
+  ctx->mass = mass;
+  ctx->c = c;
+  ctx->prec = precision;
+  ctx->conn = conn;
+  ctx->abs = ab;
+  ctx->u_identity = (mass == 0.0 && conn == DIRAC_CONN_NONE);
+  cudaGetDevice(&ctx->device);
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      dirac_status s = cuda_fail(nullptr, e, "create stream");
+      delete ctx;
+      return s;
+    }
+    ctx->own_stream = true;
+  }
+  dirac_status s = precision == DIRAC_C64 ? create_impl<float>(ctx, g_host)
+                                          : create_impl<double>(ctx, g_host);
+  if (s != DIRAC_OK) {
+    g_create_error = ctx->err;
+    dirac_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_set_state(dirac_ctx* ctx, const double* psi, int on_device) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (!psi) return fail(ctx, DIRAC_EINVAL, "psi is NULL");
+  const size_t n = npts(ctx);
+  const double* src = psi;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(ctx->staging, psi, 4 * n * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream),
+       "upload state");
+    src = ctx->staging;
+  }
+  if (ctx->prec == DIRAC_C64)
+    CK(launch_pack<float>(src, (Q4<float>*)ctx->psi, n, ctx->stream), "pack state");
+  else
+    CK(launch_pack<double>(src, (Q4<double>*)ctx->psi, n, ctx->stream), "pack state");
+  ctx->launches += 1;
+  if (!on_device) CK(cudaStreamSynchronize(ctx->stream), "upload state");
+  ctx->state_set = true;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_get_state(dirac_ctx* ctx, double* psi_out, int on_device) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (!psi_out) return fail(ctx, DIRAC_EINVAL, "psi_out is NULL");
+  if (!ctx->state_set) return fail(ctx, DIRAC_ESTATE, "no state has been set");
+  const size_t n = npts(ctx);
+  double* dst = on_device ? psi_out : ctx->staging;
+  if (ctx->prec == DIRAC_C64)
+    CK(launch_unpack<float>((const Q4<float>*)ctx->psi, dst, n, ctx->stream), "unpack state");
+  else
+    CK(launch_unpack<double>((const Q4<double>*)ctx->psi, dst, n, ctx->stream), "unpack state");
+  ctx->launches += 1;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(psi_out, ctx->staging, 4 * n * sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream),
+       "download state");
+    CK(cudaStreamSynchronize(ctx->stream), "download state");
+  }
+  return DIRAC_OK;
+}
+
+dirac_status dirac_step(dirac_ctx* ctx, long n_steps, double dt) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (n_steps < 0) return fail(ctx, DIRAC_EINVAL, "n_steps must be >= 0");
+  if (!(dt > 0.0) || !isfinite(dt)) return fail(ctx, DIRAC_EINVAL, "dt must be positive");
+  if (!ctx->state_set) return fail(ctx, DIRAC_ESTATE, "set_state must come before step");
+  if (n_steps == 0) return DIRAC_OK;
+  return ctx->prec == DIRAC_C64 ? step_impl<float>(ctx, n_steps, dt)
+                                : step_impl<double>(ctx, n_steps, dt);
+}
+
+dirac_status dirac_observables(dirac_ctx* ctx, dirac_obs* out, double* density_or_NULL) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (!out) return fail(ctx, DIRAC_EINVAL, "out is NULL");
+  if (!ctx->state_set) return fail(ctx, DIRAC_ESTATE, "no state has been set");
+  return ctx->prec == DIRAC_C64 ? observables_impl<float>(ctx, out, density_or_NULL)
+                                : observables_impl<double>(ctx, out, density_or_NULL);
+}
+
+dirac_status dirac_synchronize(dirac_ctx* ctx) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+  return DIRAC_OK;
+}
+
+const char* dirac_last_error(const dirac_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void dirac_destroy(dirac_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  free_all(ctx);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_pass) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  const int t[2] = {threads_x_pass, threads_y_pass};
+  const int L[2] = {ctx->nx, ctx->ny};
+  for (int k = 0; k < 2; ++k) {
+    if (t[k] == 0) continue;
+    if (t[k] < 32 || t[k] > 512 || (t[k] & (t[k] - 1)))
+      return fail(ctx, DIRAC_EINVAL, "threads must be 0 or a power of two in [32, 512]");
+    const int E = ctx->prec == DIRAC_C64 ? 16 : 8;
+    if (t[k] < L[k] / E) return fail(ctx, DIRAC_EINVAL, "threads below one line's worth");
+  }
+  ctx->threads_x = threads_x_pass;
+  ctx->threads_y = threads_y_pass;
+  return DIRAC_OK;
+}
+
+long dirac_launch_count(const dirac_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

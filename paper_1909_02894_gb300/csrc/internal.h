@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "common.cuh"
+#include "line_pass.cuh"
+
+namespace dgb {
+
+// Launch geometry of one fused line pass.
+struct LaunchShape {
+  int tpl;          // threads per line = L / E
+  int lpc;          // lines per CTA
+  int cs;           // CTAs per cluster
+  int npass;        // Stockham passes per FFT
+  int rl;           // radix of the last pass
+  int line_stride;  // shared-memory complex slots per line (both components, padded)
+  size_t smem;      // dynamic shared memory bytes
+  int threads;      // threads per CTA
+  int blocks;       // CTAs
+};
+
+template <typename T>
+LaunchShape line_pass_shape(int L, int n_lines, int threads_req);
+
+// Enqueues one fused line pass (MODE_STEP or MODE_DERIV). threads_req = 0 picks 256.
+template <typename T>
+cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int threads_req,
+                             cudaStream_t st);
+
+// ---- FP64 precompute (precompute.cu)
+// a1, a2, meff, w and the two log fields (packed as a complex128 spinor (f1, f2)) from the
+// metric; g == nullptr means 1.
+cudaError_t launch_metric_fields(const double* g00, const double* g11, const double* g22,
+                                 int n, double c, double mass, int conn, double* a1,
+                                 double* a2, double* meff, double* w, Q4<double>* logs,
+                                 cudaStream_t st);
+// Omega_x, Omega_y (normal layout) from the x derivative (transposed layout [nx][ny]) and
+// the y derivative (normal layout) of the log fields.
+cudaError_t launch_omega(const Q4<double>* dxT, const Q4<double>* dy, int nx, int ny,
+                         double fac, double* omx, double* omy, cudaStream_t st);
+// 1/S for grid indices of one axis (Sec. 3 profiles), real (theta = 0).
+cudaError_t launch_pml(int n, double a, int width, int type, double sigma0, double* sinv,
+                       cudaStream_t st);
+// beta1 = a1/S1 - 1 (normal layout), beta2T = a2/S2 - 1 (transposed layout), in T.
+template <typename T>
+cudaError_t launch_beta(const double* a1, const double* a2, const double* sxinv,
+                        const double* syinv, int nx, int ny, T* beta1, T* beta2T,
+                        cudaStream_t st);
+// Half-step matrices for dt: U (normal layout), U and U^2 (transposed layout), stored as
+// (c0 - 1, c1, c2, c3) in T.
+template <typename T>
+cudaError_t launch_halfstep(const double* a1, const double* a2, const double* meff,
+                            const double* omx, const double* omy, int nx, int ny, double dt,
+                            Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, cudaStream_t st);
+// Per-axis tables: twiddles exp(-2 pi i m / n); step multipliers
+// ((cos(dt xi) - 1)/n, sin(dt xi)/n) as hi/lo pairs; derivative multipliers xi/n.
+template <typename T>
+cudaError_t launch_twiddles(int n, Cx<T>* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream_t st);
+template <typename T>
+cudaError_t launch_deriv_mult(int n, double a, Q4<T>* mult, cudaStream_t st);
+
+// Tiled transpose of a [rows][cols] array of Q4<T> into [cols][rows].
+template <typename T>
+cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cudaStream_t st);
+
+// ---- state conversion and observables (observables.cu)
+// psi[k] = (p1[k], p2[k]) from a [2][n] complex128 array, and back.
+template <typename T>
+cudaError_t launch_pack(const double* src, Q4<T>* psi, size_t n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_unpack(const Q4<T>* psi, double* dst, size_t n, cudaStream_t st);
+// Per-block FP64 partial sums {norm, norm_gamma, e_re, e_im} into partials[blocks][4]
+// and the density map (if not null). dx and dy may be null (no energy).
+template <typename T>
+cudaError_t launch_observables(const Q4<T>* psi, const Q4<T>* dx, const Q4<T>* dy,
+                               const double* a1, const double* a2, const double* meff,
+                               const double* w, const double* omx, const double* omy,
+                               size_t n, double* density, double* partials, int blocks,
+                               cudaStream_t st);
+cudaError_t launch_reduce_partials(const double* partials, int blocks, double scale,
+                                   double* result, cudaStream_t st);
+int observables_blocks(size_t n);
+
+}  // namespace dgb

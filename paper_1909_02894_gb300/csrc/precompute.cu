@@ -1,0 +1,277 @@
+// FP64 precompute on the device: coefficient fields, spin connection, absorbing-layer
+// profile, half-step matrices and the per-axis FFT/k-space tables. Runs at context
+// creation (and, for U and the k-space tables, whenever dt changes); never per step.
+#include <math.h>
+
+#include "internal.h"
+
+namespace dgb {
+
+static const int TPB = 256;
+static inline int nblocks(size_t n) { return (int)((n + TPB - 1) / TPB); }
+
+// Sec. 2.2 with a diagonal static metric: a^j = c sqrt(g00/g_jj), meff = m c^2 sqrt(g00),
+// w = sqrt(g11 g22/g00) (sqrt|g| g^00, eq. l2gamma). The spin connection needs the
+// derivative of ln(w a^j) (covariant) or of ln g00 (the printed 2D form).
+__global__ void k_metric_fields(const double* g00, const double* g11, const double* g22, int n,
+                                double c, double mass, int conn, double* a1, double* a2,
+                                double* meff, double* w, Q4<double>* logs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double G00 = g00 ? g00[k] : 1.0, G11 = g11 ? g11[k] : 1.0, G22 = g22 ? g22[k] : 1.0;
+  const double A1 = c * sqrt(G00 / G11), A2 = c * sqrt(G00 / G22);
+  const double Wt = sqrt(G11 * G22 / G00);
+  a1[k] = A1;
+  a2[k] = A2;
+  meff[k] = mass * c * c * sqrt(G00);
+  w[k] = Wt;
+  double f1, f2;
+  if (conn == 1) {
+    f1 = f2 = log(G00);
+  } else {
+    f1 = log(Wt * A1);
+    f2 = log(Wt * A2);
+  }
+  logs[k] = {f1, 0.0, f2, 0.0};
+}
+
+cudaError_t launch_metric_fields(const double* g00, const double* g11, const double* g22,
+                                 int n, double c, double mass, int conn, double* a1,
+                                 double* a2, double* meff, double* w, Q4<double>* logs,
+                                 cudaStream_t st) {
+  k_metric_fields<<<nblocks(n), TPB, 0, st>>>(g00, g11, g22, n, c, mass, conn, a1, a2, meff,
+                                              w, logs);
+  return cudaGetLastError();
+}
+
+// Omega_x = fac Re d_x f1, Omega_y = fac Re d_y f2 (the real part drops the purely
+// imaginary Nyquist term of a real field's spectral derivative).
+__global__ void k_omega(const Q4<double>* dxT, const Q4<double>* dy, int nx, int ny, double fac,
+                        double* omx, double* omy) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx * ny) return;
+  const int j = k / nx, i = k - j * nx;
+  omx[k] = fac * dxT[(size_t)i * ny + j].x;
+  omy[k] = fac * dy[k].z;
+}
+
+cudaError_t launch_omega(const Q4<double>* dxT, const Q4<double>* dy, int nx, int ny,
+                         double fac, double* omx, double* omy, cudaStream_t st) {
+  k_omega<<<nblocks((size_t)nx * ny), TPB, 0, st>>>(dxT, dy, nx, ny, fac, omx, omy);
+  return cudaGetLastError();
+}
+
+// Sec. 3: S = 1 + Sigma~ (theta = 0) on the outer `width` points of each side. The depth
+// into the layer is measured from the layer's inner edge on the grid: e = (width - i) h on
+// the left (so the point x_0 = -a is exactly at |x| = L) and e = (i - n + width) h on the
+// right; with s = e - delta (delta = width h) the six profiles are
+// s0 e^2, s0 e^3, -s0/s, s0/s^2, -s0/s - s0/delta, s0/s^2 - s0/delta^2.
+// Where a singular profile is infinite, 1/S = 0.
+__global__ void k_pml(int n, double a, int width, int type, double sigma0, double* sinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = 1.0;
+  if (width > 0 && (i <= width || i >= n - width)) {
+    const double h = 2.0 * a / n;
+    const double depth = (i <= width) ? (double)(width - i) * h : (double)(i - n + width) * h;
+    const double delta = width * h;
+    const double s = depth - delta;
+    double sig = 0.0;
+    bool inf = false;
+    switch (type) {
+      case 1: sig = sigma0 * depth * depth; break;
+      case 2: sig = sigma0 * depth * depth * depth; break;
+      case 3: inf = (s == 0.0); if (!inf) sig = -sigma0 / s; break;
+      case 4: inf = (s == 0.0); if (!inf) sig = sigma0 / (s * s); break;
+      case 5: inf = (s == 0.0); if (!inf) sig = -sigma0 / s - sigma0 / delta; break;
+      case 6: inf = (s == 0.0); if (!inf) sig = sigma0 / (s * s) - sigma0 / (delta * delta); break;
+      default: break;
+    }
+    r = inf ? 0.0 : 1.0 / (1.0 + sig);
+  }
+  sinv[i] = r;
+}
+
+cudaError_t launch_pml(int n, double a, int width, int type, double sigma0, double* sinv,
+                       cudaStream_t st) {
+  k_pml<<<nblocks(n), TPB, 0, st>>>(n, a, width, type, sigma0, sinv);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_beta(const double* a1, const double* a2, const double* sxinv,
+                       const double* syinv, int nx, int ny, T* beta1, T* beta2T) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx * ny) return;
+  const int j = k / nx, i = k - j * nx;
+  beta1[k] = (T)(a1[k] * sxinv[i] - 1.0);
+  beta2T[(size_t)i * ny + j] = (T)(a2[k] * syinv[j] - 1.0);
+}
+
+template <typename T>
+cudaError_t launch_beta(const double* a1, const double* a2, const double* sxinv,
+                        const double* syinv, int nx, int ny, T* beta1, T* beta2T,
+                        cudaStream_t st) {
+  k_beta<T><<<nblocks((size_t)nx * ny), TPB, 0, st>>>(a1, a2, sxinv, syinv, nx, ny, beta1,
+                                                      beta2T);
+  return cudaGetLastError();
+}
+
+// exp(v.sigma) = C(z) I + S(z) v.sigma with z = v.v (Sec. 4.1 eq. exp_dirac in the
+// complex-argument form), C = cosh sqrt z, S = sinh sqrt z / sqrt z; here v1, v2 are real
+// and v3 = -i dt/2 meff, so z is real. Returns (C - 1, S v1, S v2, -dt/2 meff S) with C - 1
+// written as a squared half-angle sine to keep it accurate when z is small.
+__device__ inline void pauli_exp(double v1, double v2, double hm, double* out) {
+  const double z = v1 * v1 + v2 * v2 - hm * hm;
+  double cm1, S;
+  if (fabs(z) < 1e-8) {
+    cm1 = z * (0.5 + z * (1.0 / 24.0 + z * (1.0 / 720.0)));
+    S = 1.0 + z * (1.0 / 6.0 + z * (1.0 / 120.0 + z * (1.0 / 5040.0)));
+  } else if (z > 0.0) {
+    const double r = sqrt(z);
+    const double sh = sinh(0.5 * r);
+    cm1 = 2.0 * sh * sh;
+    S = sinh(r) / r;
+  } else {
+    const double r = sqrt(-z);
+    const double sn = sin(0.5 * r);
+    cm1 = -2.0 * sn * sn;
+    S = sin(r) / r;
+  }
+  out[0] = cm1;
+  out[1] = S * v1;
+  out[2] = S * v2;
+  out[3] = -hm * S;
+}
+
+template <typename T>
+__global__ void k_halfstep(const double* a1, const double* a2, const double* meff,
+                           const double* omx, const double* omy, int nx, int ny, double dt,
+                           Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nx * ny) return;
+  const int j = k / nx, i = k - j * nx;
+  // exponent -i dt/2 (meff sigma_z + F), F = -i (a1 Omx sigma_x + a2 Omy sigma_y)
+  const double v1 = -0.5 * dt * a1[k] * omx[k];
+  const double v2 = -0.5 * dt * a2[k] * omy[k];
+  const double hm = 0.5 * dt * meff[k];
+  double u[4], u2[4];
+  pauli_exp(v1, v2, hm, u);
+  pauli_exp(2.0 * v1, 2.0 * v2, 2.0 * hm, u2);
+  const Q4<T> U = {(T)u[0], (T)u[1], (T)u[2], (T)u[3]};
+  const Q4<T> U2 = {(T)u2[0], (T)u2[1], (T)u2[2], (T)u2[3]};
+  u_n[k] = U;
+  u_t[(size_t)i * ny + j] = U;
+  u2_t[(size_t)i * ny + j] = U2;
+}
+
+template <typename T>
+cudaError_t launch_halfstep(const double* a1, const double* a2, const double* meff,
+                            const double* omx, const double* omy, int nx, int ny, double dt,
+                            Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, cudaStream_t st) {
+  k_halfstep<T><<<nblocks((size_t)nx * ny), TPB, 0, st>>>(a1, a2, meff, omx, omy, nx, ny, dt,
+                                                          u_n, u_t, u2_t);
+  return cudaGetLastError();
+}
+
+// hi/lo split of an FP64 value into the table type.
+template <typename T>
+__device__ inline void split(double v, T* hi, T* lo) {
+  const T h = (T)v;
+  *hi = h;
+  *lo = (T)(v - (double)h);
+}
+
+template <typename T>
+__global__ void k_twiddles(int n, Cx<T>* tw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double s, c;
+  sincospi(2.0 * m / n, &s, &c);
+  tw[m] = {(T)c, (T)(-s)};
+}
+
+template <typename T>
+cudaError_t launch_twiddles(int n, Cx<T>* tw, cudaStream_t st) {
+  k_twiddles<T><<<nblocks(n), TPB, 0, st>>>(n, tw);
+  return cudaGetLastError();
+}
+
+// Sec. 5: FFT index q -> p = q (q < n/2) or q - n, xi = p pi / a. The step multiplier is
+// exp(-i dt xi sigma) - I = (cos - 1) I - i sin sigma, scaled by the inverse FFT's 1/n.
+template <typename T>
+__global__ void k_step_mult(int n, double a, double dt, Q4<T>* mult) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int p = q < n / 2 ? q : q - n;
+  const double th = dt * (p * (M_PI / a));
+  const double hs = sin(0.5 * th);
+  const double cm1 = -2.0 * hs * hs / n;
+  const double sn = sin(th) / n;
+  Q4<T> r;
+  split<T>(cm1, &r.x, &r.y);
+  split<T>(sn, &r.z, &r.w);
+  mult[q] = r;
+}
+
+template <typename T>
+cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream_t st) {
+  k_step_mult<T><<<nblocks(n), TPB, 0, st>>>(n, a, dt, mult);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_deriv_mult(int n, double a, Q4<T>* mult) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int p = q < n / 2 ? q : q - n;
+  Q4<T> r;
+  r.x = r.y = (T)0;
+  split<T>(p * (M_PI / a) / n, &r.z, &r.w);
+  mult[q] = r;
+}
+
+template <typename T>
+cudaError_t launch_deriv_mult(int n, double a, Q4<T>* mult, cudaStream_t st) {
+  k_deriv_mult<T><<<nblocks(n), TPB, 0, st>>>(n, a, mult);
+  return cudaGetLastError();
+}
+
+// 32 x 32 tiles through shared memory; one padding column avoids bank conflicts.
+template <typename T>
+__global__ void k_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols) {
+  __shared__ Q4<T> tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int r = r0 + dy, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[dy][threadIdx.x] = in[(size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int dy = threadIdx.y; dy < 32; dy += blockDim.y) {
+    const int c = c0 + dy, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(size_t)c * rows + r] = tile[threadIdx.x][dy];
+  }
+}
+
+template <typename T>
+cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_transpose<T><<<grid, dim3(32, 8), 0, st>>>(in, out, rows, cols);
+  return cudaGetLastError();
+}
+
+#define INST(T)                                                                              \
+  template cudaError_t launch_beta<T>(const double*, const double*, const double*,          \
+                                      const double*, int, int, T*, T*, cudaStream_t);        \
+  template cudaError_t launch_halfstep<T>(const double*, const double*, const double*,      \
+                                          const double*, const double*, int, int, double,    \
+                                          Q4<T>*, Q4<T>*, Q4<T>*, cudaStream_t);             \
+  template cudaError_t launch_twiddles<T>(int, Cx<T>*, cudaStream_t);                         \
+  template cudaError_t launch_step_mult<T>(int, double, double, Q4<T>*, cudaStream_t);        \
+  template cudaError_t launch_deriv_mult<T>(int, double, Q4<T>*, cudaStream_t);               \
+  template cudaError_t launch_transpose<T>(const Q4<T>*, Q4<T>*, int, int, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace dgb
