@@ -222,7 +222,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w, prec_name, bytes_pt = workload(args.workload)
     prec = D.DIRAC_C64 if prec_name == "c64" else D.DIRAC_C128
-    stream = torch.cuda.current_stream()
+    # A dedicated stream: the default stream's handle is 0, which the ABI reads as
+    # "create a private stream", and events must be recorded where the kernels run.
+    stream = torch.cuda.Stream()
     sim = D.Simulation(w, precision=prec, stream=stream.cuda_stream)
     sim.set_state(w.psi0)
     pts = w.nx * w.ny
