@@ -134,9 +134,10 @@ const char *dirac_last_error(const dirac_ctx *ctx);
 /* Releases the context and all its device memory. NULL is allowed. */
 void dirac_destroy(dirac_ctx *ctx);
 
-/* Launch parameters of the two fused passes (each pass: FFT along a line, k-space
- * multiply, inverse FFT, combine, transposed store). threads: threads per CTA for that
- * line length; 0 = the built-in default. Used by the autotuner. */
+/* CTA shape of the two fused passes (each pass: FFT along a line, k-space multiply,
+ * inverse FFT, combine, transposed store): about 256 or 512 threads per CTA for that
+ * pass's line length; 0 = the default (512). Lines of 128 points or fewer and 4096-point
+ * lines have one shape only. Used by the autotuner. DIRAC_EINVAL for other values. */
 dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_pass);
 
 /* Number of kernel launches this context has enqueued so far (for accounting). */

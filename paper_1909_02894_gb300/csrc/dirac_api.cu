@@ -127,11 +127,11 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   for (long s = 0; s < n; ++s) {
     ax.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
     ax.u_store = nullptr;
-    CK(launch_line_pass<T>(ax, MODE_STEP, ctx->threads_x, ctx->stream), "x pass");
+    CK(launch_line_pass<T>(ax, MODE_STEP, ctx->threads_x == 256 ? 0 : 1, ctx->stream), "x pass");
     ay.u_load = nullptr;
     ay.u_store = ctx->u_identity ? nullptr
                                  : (const Q4<T>*)(s + 1 == n ? ctx->u_t : ctx->u2_t);
-    CK(launch_line_pass<T>(ay, MODE_STEP, ctx->threads_y, ctx->stream), "y pass");
+    CK(launch_line_pass<T>(ay, MODE_STEP, ctx->threads_y == 256 ? 0 : 1, ctx->stream), "y pass");
     ctx->launches += 2;
   }
   return DIRAC_OK;
@@ -461,14 +461,9 @@ void dirac_destroy(dirac_ctx* ctx) {
 dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_pass) {
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
   const int t[2] = {threads_x_pass, threads_y_pass};
-  const int L[2] = {ctx->nx, ctx->ny};
-  for (int k = 0; k < 2; ++k) {
-    if (t[k] == 0) continue;
-    if (t[k] < 32 || t[k] > 512 || (t[k] & (t[k] - 1)))
-      return fail(ctx, DIRAC_EINVAL, "threads must be 0 or a power of two in [32, 512]");
-    const int E = ctx->prec == DIRAC_C64 ? 16 : 8;
-    if (t[k] < L[k] / E) return fail(ctx, DIRAC_EINVAL, "threads below one line's worth");
-  }
+  for (int k = 0; k < 2; ++k)
+    if (t[k] != 0 && t[k] != 256 && t[k] != 512)
+      return fail(ctx, DIRAC_EINVAL, "threads must be 0 (default), 256 or 512");
   ctx->threads_x = threads_x_pass;
   ctx->threads_y = threads_y_pass;
   return DIRAC_OK;

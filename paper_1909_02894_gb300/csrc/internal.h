@@ -3,32 +3,17 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <string>
 
 #include "common.cuh"
 #include "line_pass.cuh"
 
 namespace dgb {
 
-// Launch geometry of one fused line pass.
-struct LaunchShape {
-  int tpl;          // threads per line = L / E
-  int lpc;          // lines per CTA
-  int cs;           // CTAs per cluster
-  int npass;        // Stockham passes per FFT
-  int rl;           // radix of the last pass
-  int line_stride;  // shared-memory complex slots per line (both components, padded)
-  size_t smem;      // dynamic shared memory bytes
-  int threads;      // threads per CTA
-  int blocks;       // CTAs
-};
-
+// Enqueues one fused line pass (MODE_STEP or MODE_DERIV). opt selects the CTA shape:
+// 0 = about 256 threads per CTA, 1 = 512 threads (step mode only).
 template <typename T>
-LaunchShape line_pass_shape(int L, int n_lines, int threads_req);
-
-// Enqueues one fused line pass (MODE_STEP or MODE_DERIV). threads_req = 0 picks 256.
-template <typename T>
-cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int threads_req,
-                             cudaStream_t st);
+cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st);
 
 // ---- FP64 precompute (precompute.cu)
 // a1, a2, meff, w and the two log fields (packed as a complex128 spinor (f1, f2)) from the

@@ -6,89 +6,80 @@
 
 namespace dgb {
 
-template <typename T>
-constexpr int elems_per_thread() { return sizeof(T) == 4 ? 16 : 8; }
-// Lines gathered per transposed-store segment: 8 x 16 B (c64) or 4 x 32 B (c128) = 128 B.
-template <typename T>
-constexpr int seg_lines() { return sizeof(T) == 4 ? 8 : 4; }
-
-inline int ilog2(int v) {
-  int l = 0;
-  while ((1 << l) < v) ++l;
-  return l;
-}
-
-template <typename T>
-LaunchShape line_pass_shape(int L, int n_lines, int threads_req) {
-  constexpr int E = elems_per_thread<T>();
-  LaunchShape s{};
-  s.tpl = L / E;
-  const int thr = threads_req > 0 ? threads_req : 256;
-  int lpc = thr / s.tpl;
-  if (lpc < 1) lpc = 1;
-  while (lpc & (lpc - 1)) lpc &= lpc - 1;  // power of two
-  if (lpc > n_lines) lpc = n_lines;
-  const int G = seg_lines<T>();
-  s.cs = lpc >= G ? 1 : G / lpc;
-  while (s.cs > 1 && lpc * s.cs > n_lines) s.cs >>= 1;
-  s.lpc = lpc;
-  const int l = ilog2(L), e = ilog2(E);
-  s.npass = (l + e - 1) / e;
-  s.rl = 1 << (l - (s.npass - 1) * e);
-  const int plen = Pad<T>::len(L);
-  s.line_stride = 2 * plen + (s.tpl < 16 ? (((s.tpl - 2 * plen) % 16) + 16) % 16 : 0);
-  const size_t fft_bytes = (size_t)lpc * s.line_stride * sizeof(Cx<T>);
-  const size_t stage_bytes = (size_t)lpc * (L + 1) * sizeof(Q4<T>);
-  s.smem = fft_bytes > stage_bytes ? fft_bytes : stage_bytes;
-  s.threads = lpc * s.tpl;
-  s.blocks = n_lines / lpc;
-  return s;
-}
-
-template <typename T, int MODE>
-static cudaError_t launch_mode(const LinePassArgs<T>& a0, int threads_req, cudaStream_t st) {
-  constexpr int E = elems_per_thread<T>();
-  LinePassArgs<T> a = a0;
-  const LaunchShape s = line_pass_shape<T>(a.L, a.n_lines, threads_req);
-  if (s.threads > 512 || s.threads < 1 || a.n_lines % (s.lpc * s.cs) != 0)
-    return cudaErrorInvalidConfiguration;
-  a.lpc = s.lpc;
-  a.cs = s.cs;
-  auto kern = line_pass_kernel<T, E, MODE>;
-  // The dynamic shared-memory limit is a per-device function attribute; remember what was
-  // set for each device so the hot loop does not repeat the call.
-  static size_t configured[64] = {0};
+template <typename T, int L, int LPC, int MODE>
+static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
+  using Gm = Geo<T, L, LPC>;
+  if (a.n_lines % Gm::GL != 0 || a.n_lines < Gm::GL) return cudaErrorInvalidValue;
+  auto kern = line_pass_kernel<T, L, LPC, MODE>;
+  // Function attributes are per device; set them once per device for this kernel.
+  static bool configured[64] = {false};
   int dev = 0;
-  cudaGetDevice(&dev);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (s.smem > 48 * 1024 && s.smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)s.smem);
+  if (!configured[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Gm::SMEM);
     if (e != cudaSuccess) return e;
-    configured[dev] = s.smem;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    configured[dev] = true;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(s.blocks, 1, 1);
-  cfg.blockDim = dim3(s.threads, 1, 1);
-  cfg.dynamicSmemBytes = s.smem;
+  cfg.gridDim = dim3(a.n_lines / LPC, 1, 1);
+  cfg.blockDim = dim3(Gm::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = Gm::SMEM;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
-  if (s.cs > 1) {
+  if (Gm::CS > 1) {
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = s.cs;
+    attr[0].val.clusterDim.x = Gm::CS;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, kern, a, s.npass, s.rl, s.line_stride);
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// Two CTA shapes per line length: opt 0 (about 256 threads) and opt 1 (512 threads);
+// lines of 128 points or fewer use 16 lines per CTA, 4096-point lines one line of 512
+// threads.
+template <typename T, int MODE>
+static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) {
+  const bool big = (MODE == MODE_STEP) && opt != 0;
+  switch (a.L) {
+    case 16: return launch_one<T, 16, 16, MODE>(a, st);
+    case 32: return launch_one<T, 32, 16, MODE>(a, st);
+    case 64: return launch_one<T, 64, 16, MODE>(a, st);
+    case 128: return launch_one<T, 128, 16, MODE>(a, st);
+    case 4096: return launch_one<T, 4096, 1, MODE>(a, st);
+    default: break;
+  }
+  if constexpr (MODE == MODE_STEP) {
+    if (big) {
+      switch (a.L) {
+        case 256: return launch_one<T, 256, 16, MODE>(a, st);
+        case 512: return launch_one<T, 512, 8, MODE>(a, st);
+        case 1024: return launch_one<T, 1024, 4, MODE>(a, st);
+        case 2048: return launch_one<T, 2048, 2, MODE>(a, st);
+        default: return cudaErrorInvalidValue;
+      }
+    }
+  }
+  switch (a.L) {
+    case 256: return launch_one<T, 256, 8, MODE>(a, st);
+    case 512: return launch_one<T, 512, 4, MODE>(a, st);
+    case 1024: return launch_one<T, 1024, 2, MODE>(a, st);
+    case 2048: return launch_one<T, 2048, 1, MODE>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>
-cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int threads_req,
-                             cudaStream_t st) {
-  if (mode == MODE_DERIV) return launch_mode<T, MODE_DERIV>(a, threads_req, st);
-  return launch_mode<T, MODE_STEP>(a, threads_req, st);
+cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st) {
+  if (mode == MODE_DERIV) return dispatch<T, MODE_DERIV>(a, 0, st);
+  return dispatch<T, MODE_STEP>(a, opt, st);
 }
 
 }  // namespace dgb

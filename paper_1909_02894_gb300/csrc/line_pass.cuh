@@ -1,22 +1,27 @@
 // Fused line pass: one direction of one Scheme II step for a block of lines.
 //
-// For every line (a row of the input array, length L) and both spinor components:
-//   forward FFT along the line  ->  k-space multiply  ->  inverse FFT  ->  pointwise
-//   epilogue  ->  store TRANSPOSED (out[i][line]).
+// For every line (a row of the input array, length L):
+//   forward FFT along the line -> k-space multiply -> inverse FFT -> pointwise epilogue
+//   -> store TRANSPOSED (out[i][line]).
 // Two passes make a step: the x pass reads psi[ny][nx] and writes psiT[nx][ny]; the
 // y pass reads psiT and writes psi back. Both therefore read whole contiguous lines.
 //
-// Step mode (Sec. 5.2 eq. second_scheme, written as a deviation from identity):
-//   D = F^-1[ (exp(-i dt xi sigma_j) - I) / L  F psi ]      (unnormalised inverse FFT)
-//   psi_new = psi + b D = psi + D + (b - 1) D,  then optionally U psi_new
-// which equals b Xi + (1 - b) psi with Xi = F^-1[exp(-i dt xi sigma_j) F psi].
-// Derivative mode (Sec. 5 eq. trick): out = F^-1[ i xi / L  F psi ] per component.
+// Step mode (Sec. 5.2 eq. second_scheme). In the eigenbasis of sigma_j the k-space
+// operator exp(-i dt xi sigma_j) is diagonal: phi_+- = psi_1 +- psi_2 (sigma_x) or
+// psi_1 -+ i psi_2 (sigma_y) are multiplied by exp(-+ i dt xi). Each eigencomponent is a
+// scalar FFT -> multiply -> inverse FFT chain, computed by its own thread:
+//   D_+- = F^-1[ (exp(-+ i dt xi) - 1) / (2L) F phi_+- ]
+//   D    = (D_+ + D_-, D_+ - D_-)  (sigma_x)   or   (D_+ + D_-, i (D_+ - D_-))  (sigma_y)
+//   psi_new = psi + D + (b - 1) D,  optionally followed by U psi_new
+// which equals b Xi + (1 - b) psi with Xi = F^-1[exp(-i dt xi sigma_j) F psi]; writing it
+// as a deviation from identity keeps FP32 rounding proportional to |exp(..) - 1|.
+// Derivative mode (Sec. 5 eq. trick): out_c = F^-1[ i xi / L  F psi_c ] per component.
 //
-// FFT: radix-E Stockham autosort in registers with shared-memory exchanges between
-// passes. Thread j of a line holds elements j + m L/E (m < E) of both components; that
-// index set is the input of the first pass and the output of the last one for any
-// radix sequence, so the global load, the k-space multiply and the global store all
-// happen in registers.
+// FFT: radix-16 Stockham autosort. Thread (j, c) of a line holds elements j + m L/16
+// (m < 16) of component c; that index set is the input of the first pass and the output
+// of the last one for any radix sequence, so the global load, the k-space multiply and
+// the epilogue happen in registers and only the passes in between go through shared
+// memory. The line length L is a template parameter: all index arithmetic folds.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -32,17 +37,15 @@ template <typename T>
 struct LinePassArgs {
   const Q4<T>* in;      // [n_lines][L] spinor points
   Q4<T>* out;           // [L][n_lines] spinor points (transposed)
-  int L;                // line length = FFT size (power of two, >= 16)
+  int L;                // line length = FFT size (power of two, 16..4096)
   int n_lines;          // lines in the input = row length of the output
   int sigma;            // 0: sigma_x (x pass), 1: sigma_y (y pass)
   const Cx<T>* tw;      // tw[m] = exp(-2 pi i m / L), m < L
-  const Q4<T>* mult;    // per k index q: step (c-1 hi, c-1 lo, s hi, s lo) / L;
+  const Q4<T>* mult;    // per k index q: step ((cos - 1) hi, lo, sin hi, lo) / (2L);
                         // derivative (0, 0, xi hi, xi lo) / L
   const T* beta;        // b - 1 per input point, or nullptr (b = 1)
   const Q4<T>* u_load;  // U applied to psi when it is read, or nullptr
   const Q4<T>* u_store; // U applied to psi_new before the store, or nullptr
-  int lpc;              // lines per CTA
-  int cs;               // CTAs per cluster (1 = no cluster)
 };
 
 // Read-only cached loads of the table types.
@@ -67,35 +70,32 @@ __device__ __forceinline__ Q4<double> ldg_q4(const Q4<double>* p) {
 // ---------------------------------------------------------------- small DFTs
 template <typename T, bool INV>
 __device__ __forceinline__ void dft2(Cx<T>& a, Cx<T>& b) {
-  Cx<T> t = a;
+  const Cx<T> t = a;
   a = cadd(t, b);
   b = csub(t, b);
 }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft4(Cx<T>& x0, Cx<T>& x1, Cx<T>& x2, Cx<T>& x3) {
-  Cx<T> a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
-  Cx<T> jd = INV ? mul_i(d) : mul_mi(d);
+  const Cx<T> a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
+  const Cx<T> jd = INV ? mul_i(d) : mul_mi(d);
   x0 = cadd(a, c);
   x2 = csub(a, c);
   x1 = cadd(b, jd);
   x3 = csub(b, jd);
 }
 
-// multiply by exp(-+ 2 pi i m / 16) (forward: minus)
+// multiply by exp(-+ 2 pi i M / 16) (forward: minus); cos/sin of pi M / 8 as constants
 template <typename T, bool INV, int M>
 __device__ __forceinline__ Cx<T> w16(Cx<T> a) {
-  constexpr double PI = 3.14159265358979323846264338327950288;
-  // cos and sin of pi M / 8 folded at compile time
-  constexpr double c = (M == 0) ? 1.0 : (M == 1) ? 0.92387953251128675613 : (M == 2) ? 0.70710678118654752440
-                     : (M == 3) ? 0.38268343236508977173 : (M == 4) ? 0.0 : (M == 6) ? -0.70710678118654752440
+  constexpr double c = (M == 1) ? 0.92387953251128675613 : (M == 2) ? 0.70710678118654752440
+                     : (M == 3) ? 0.38268343236508977173 : (M == 6) ? -0.70710678118654752440
                      : (M == 9) ? -0.92387953251128675613 : 0.0;
-  constexpr double s = (M == 0) ? 0.0 : (M == 1) ? 0.38268343236508977173 : (M == 2) ? 0.70710678118654752440
-                     : (M == 3) ? 0.92387953251128675613 : (M == 4) ? 1.0 : (M == 6) ? 0.70710678118654752440
+  constexpr double s = (M == 1) ? 0.38268343236508977173 : (M == 2) ? 0.70710678118654752440
+                     : (M == 3) ? 0.92387953251128675613 : (M == 6) ? 0.70710678118654752440
                      : (M == 9) ? -0.38268343236508977173 : 0.0;
-  (void)PI;
-  if (M == 0) return a;
-  if (M == 4) return INV ? mul_i(a) : mul_mi(a);
+  if constexpr (M == 0) return a;
+  if constexpr (M == 4) return INV ? mul_i(a) : mul_mi(a);
   const Cx<T> w = {T(c), INV ? T(s) : T(-s)};
   return cmul(a, w);
 }
@@ -115,11 +115,27 @@ __device__ __forceinline__ void dft8(Cx<T> (&x)[8]) {
   x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
 }
 
-template <typename T, bool INV>
-__device__ __forceinline__ void dft16(Cx<T> (&x)[16]) {
+// Radix-16 butterfly with an optional input twiddle W^(t step) on element t (t >= 1),
+// loaded from the table just before the inner DFT4 that consumes it, so that only four
+// twiddles are live at a time.
+template <typename T, bool INV, bool TW>
+__device__ __forceinline__ void dft16(Cx<T> (&x)[16], const Cx<T>* __restrict__ tw = nullptr,
+                                      int step = 0) {
   // 16 = 4 x 4: inner DFT4 over n1 of x[4 n1 + n2], twiddle W16^(n2 k1), outer DFT4.
 #pragma unroll
-  for (int n2 = 0; n2 < 4; ++n2) dft4<T, INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+  for (int n2 = 0; n2 < 4; ++n2) {
+    if constexpr (TW) {
+#pragma unroll
+      for (int n1 = 0; n1 < 4; ++n1) {
+        const int t = 4 * n1 + n2;
+        if (t == 0) continue;
+        const Cx<T> w = ldg_cx(tw + t * step);
+        x[t] = INV ? cmulc(x[t], w) : cmul(x[t], w);
+      }
+      asm volatile("" ::: "memory");
+    }
+    dft4<T, INV>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+  }
   x[5] = w16<T, INV, 1>(x[5]);
   x[9] = w16<T, INV, 2>(x[9]);
   x[13] = w16<T, INV, 3>(x[13]);
@@ -150,237 +166,287 @@ __device__ __forceinline__ void dftR(Cx<T> (&x)[R]) {
   } else if constexpr (R == 8) {
     dft8<T, INV>(x);
   } else {
-    dft16<T, INV>(x);
+    dft16<T, INV, false>(x);
   }
 }
 
-// Shared-memory padding: one slot every PADK complex slots keeps the strided Stockham
-// writes free of bank conflicts (8-byte slots: 16 per 128 B; 16-byte slots: 8).
-template <typename T>
-struct Pad {
-  static constexpr int K = (sizeof(T) == 4) ? 16 : 8;
-  static constexpr int SH = (sizeof(T) == 4) ? 4 : 3;
-  __device__ __forceinline__ static int idx(int i) { return i + (i >> SH); }
-  __host__ __device__ static int len(int L) { return L + L / K; }
+// ------------------------------------------------------------- geometry
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+// Compile-time launch geometry for line length L and LPC lines per CTA.
+// Shared memory per line: two components of P = L + L/16 padded slots (one pad slot per
+// 16 keeps the strided Stockham writes conflict-free), the second component offset by
+// half a 128-B bank row so that the two threads of a point pair never collide, plus a
+// small line pad for short lines. A CPU model of every access pattern (all L, both
+// precisions, 128..512 threads) finds no bank conflicts with these offsets.
+template <typename T, int L_, int LPC_>
+struct Geo {
+  static constexpr int L = L_;
+  static constexpr int LPC = LPC_;
+  static constexpr int E = 16;                  // elements per thread
+  static constexpr int J = L / E;               // index groups per line
+  static constexpr int TPL = 2 * J;             // threads per line (two components)
+  static constexpr int THREADS = LPC * TPL;
+  static constexpr int B = sizeof(T) == 4 ? 16 : 8;   // slots per 128 B
+  static constexpr int P = L + L / 16;
+  static constexpr int CM = (sizeof(T) == 8 && L == 32) ? 2 : B / 2;
+  static constexpr int COMP = P + (((CM - P % B) % B) + B) % B;
+  static constexpr int EXTRA = (sizeof(T) == 4 && L == 32) ? 2 : (sizeof(T) == 4 && L == 64) ? 4 : 0;
+  static constexpr int STRIDE = 2 * COMP + EXTRA;
+  static constexpr int G = sizeof(T) == 4 ? 8 : 4;    // lines per 128-B output segment
+  static constexpr int CS = LPC >= G ? 1 : G / LPC;   // CTAs per cluster
+  static constexpr int GL = LPC * CS;                  // lines gathered per output segment
+  static constexpr int LOG2L = ilog2c(L);
+  static constexpr int NPASS = (LOG2L + 3) / 4;
+  static constexpr int RL = 1 << (LOG2L - (NPASS - 1) * 4);
+  static constexpr size_t FFT_BYTES = (size_t)LPC * STRIDE * sizeof(Cx<T>);
+  static constexpr size_t STAGE_BYTES = (size_t)LPC * (L + 1) * sizeof(Q4<T>);
+  static constexpr size_t SMEM = FFT_BYTES > STAGE_BYTES ? FFT_BYTES : STAGE_BYTES;
+  static constexpr int NIT = (L / CS) * GL / THREADS;  // transposed-store items per thread
+  static_assert((L & (L - 1)) == 0 && L >= 16, "L must be a power of two >= 16");
+  static_assert(THREADS <= 512, "at most 512 threads per CTA");
+  static_assert((L / CS) * GL == NIT * THREADS, "store items must divide evenly");
 };
 
-// One radix-R Stockham pass on the registers of one thread (both components):
-// butterfly u (u < E/R) works on index s = j + u L/E, reads v[u + t E/R] (t < R),
-// twiddles by W_{Ns R}^{t k} with k = s mod Ns and applies the R-point DFT.
-template <typename T, int E, int R, bool INV>
-__device__ __forceinline__ void stockham_pass(Cx<T> (&v1)[E], Cx<T> (&v2)[E], int j, int L,
-                                              int Ns, const Cx<T>* __restrict__ tw) {
-  constexpr int NB = E / R;
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+
+// ------------------------------------------------------------- Stockham passes
+// Butterfly u (u < 16/R) works on index s = j + u L/16 and elements v[u + t 16/R]
+// (t < R): twiddle by W_{NS R}^{t k} with k = s mod NS, then the R-point DFT.
+template <typename T, int L, int R, int NS, bool INV>
+__device__ __forceinline__ void pass_compute(Cx<T> (&v)[16], int j, const Cx<T>* __restrict__ tw) {
+  constexpr int NB = 16 / R, J = L / 16;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
-    const int s = j + u * (L / E);
-    const int k = s & (Ns - 1);
-    Cx<T> x1[R], x2[R];
+    Cx<T> x[R];
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      x1[t] = v1[u + t * NB];
-      x2[t] = v2[u + t * NB];
-    }
-    if (Ns > 1) {
-      const int step = k * (L / (Ns * R));
+    for (int t = 0; t < R; ++t) x[t] = v[u + t * NB];
+    if constexpr (NS > 1 && R == 16) {
+      const int k = (j + u * J) & (NS - 1);
+      dft16<T, INV, true>(x, tw, k * (L / (NS * R)));
+    } else {
+      if constexpr (NS > 1) {
+        const int k = (j + u * J) & (NS - 1);
+        const int step = k * (L / (NS * R));
 #pragma unroll
-      for (int t = 1; t < R; ++t) {
-        const Cx<T> w = ldg_cx(tw + t * step);
-        if (INV) {
-          x1[t] = cmulc(x1[t], w);
-          x2[t] = cmulc(x2[t], w);
-        } else {
-          x1[t] = cmul(x1[t], w);
-          x2[t] = cmul(x2[t], w);
+        for (int t = 1; t < R; ++t) {
+          const Cx<T> w = ldg_cx(tw + t * step);
+          x[t] = INV ? cmulc(x[t], w) : cmul(x[t], w);
         }
       }
+      dftR<T, R, INV>(x);
     }
-    dftR<T, R, INV>(x1);
-    dftR<T, R, INV>(x2);
 #pragma unroll
-    for (int t = 0; t < R; ++t) {
-      v1[u + t * NB] = x1[t];
-      v2[u + t * NB] = x2[t];
-    }
+    for (int t = 0; t < R; ++t) v[u + t * NB] = x[t];
   }
 }
 
-// Write the outputs of a radix-R pass to shared memory: output of (u, t) goes to
-// (s - k) R + k + t Ns.
-template <typename T, int E, int R>
-__device__ __forceinline__ void stockham_store(const Cx<T> (&v1)[E], const Cx<T> (&v2)[E],
-                                               Cx<T>* b1, Cx<T>* b2, int j, int L, int Ns) {
-  constexpr int NB = E / R;
+// Output (u, t) of a pass goes to index (s - k) R + k + t NS (padded).
+template <typename T, int L, int R, int NS>
+__device__ __forceinline__ void pass_store(const Cx<T> (&v)[16], Cx<T>* buf, int j) {
+  constexpr int NB = 16 / R, J = L / 16;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
-    const int s = j + u * (L / E);
-    const int k = s & (Ns - 1);
-    const int base = (s - k) * R + k;
+    const int s = j + u * J;
+    const int k = s & (NS - 1);
+    const int base = spad((s - k) * R + k);
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      const int o = Pad<T>::idx(base + t * Ns);
-      b1[o] = v1[u + t * NB];
-      b2[o] = v2[u + t * NB];
+      // NS = 1 only in the first pass, which is radix 16, so base is a multiple of 17
+      // there; otherwise NS is a multiple of 16 and each step adds NS + NS/16 slots.
+      const int o = (NS == 1) ? base + t : base + t * (NS + NS / 16);
+      buf[o] = v[u + t * NB];
     }
   }
 }
 
-template <typename T, int E, bool INV>
-__device__ __forceinline__ void run_pass(int R, Cx<T> (&v1)[E], Cx<T> (&v2)[E], int j, int L,
-                                         int Ns, const Cx<T>* tw) {
-  if constexpr (E == 16) {
-    if (R == 16) { stockham_pass<T, E, 16, INV>(v1, v2, j, L, Ns, tw); return; }
-  }
-  if (R == 8) { stockham_pass<T, E, 8, INV>(v1, v2, j, L, Ns, tw); return; }
-  if (R == 4) { stockham_pass<T, E, 4, INV>(v1, v2, j, L, Ns, tw); return; }
-  stockham_pass<T, E, 2, INV>(v1, v2, j, L, Ns, tw);
-}
-
-template <typename T, int E>
-__device__ __forceinline__ void run_store(int R, const Cx<T> (&v1)[E], const Cx<T> (&v2)[E],
-                                          Cx<T>* b1, Cx<T>* b2, int j, int L, int Ns) {
-  if constexpr (E == 16) {
-    if (R == 16) { stockham_store<T, E, 16>(v1, v2, b1, b2, j, L, Ns); return; }
-  }
-  if (R == 8) { stockham_store<T, E, 8>(v1, v2, b1, b2, j, L, Ns); return; }
-  if (R == 4) { stockham_store<T, E, 4>(v1, v2, b1, b2, j, L, Ns); return; }
-  stockham_store<T, E, 2>(v1, v2, b1, b2, j, L, Ns);
-}
-
-template <typename T, int E>
-__device__ __forceinline__ void smem_load(Cx<T> (&v1)[E], Cx<T> (&v2)[E], const Cx<T>* b1,
-                                          const Cx<T>* b2, int j, int L) {
+template <typename T, int L>
+__device__ __forceinline__ void pass_load(Cx<T> (&v)[16], const Cx<T>* buf, int j) {
+  constexpr int J = L / 16;
+  if constexpr (J % 16 == 0) {
+    const int b = spad(j);
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int o = Pad<T>::idx(j + m * (L / E));
-    v1[m] = b1[o];
-    v2[m] = b2[o];
+    for (int m = 0; m < 16; ++m) v[m] = buf[b + m * (J + J / 16)];
+  } else {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = buf[spad(j + m * J)];
   }
 }
 
-// Full FFT (forward or inverse, unnormalised) of the E-element register sets of a line.
-// On entry v holds elements j + m L/E of the input; on exit the same indices of the
-// output. Passes: radix E first, then the remaining radix rl last; each pass but the last
-// goes through shared memory (b1, b2 per component). With the small radix last and the
-// padded layout every shared-memory access pattern is free of bank conflicts.
-template <typename T, int E, bool INV>
-__device__ __forceinline__ void line_fft(Cx<T> (&v1)[E], Cx<T> (&v2)[E], Cx<T>* b1, Cx<T>* b2,
-                                         int j, int L, int npass, int rl, const Cx<T>* tw) {
-  int Ns = 1;
-  for (int p = 0; p < npass; ++p) {
-    const int R = (p + 1 == npass) ? rl : E;
-    run_pass<T, E, INV>(R, v1, v2, j, L, Ns, tw);
-    if (p + 1 < npass) {
-      __syncthreads();  // everyone has finished reading the buffer
-      run_store<T, E>(R, v1, v2, b1, b2, j, L, Ns);
-      __syncthreads();
-      smem_load<T, E>(v1, v2, b1, b2, j, L);
-    }
-    Ns *= R;
+template <typename T, int L, bool INV, int P = 0, int NS = 1>
+__device__ __forceinline__ void fft_passes(Cx<T> (&v)[16], Cx<T>* buf, int j, const Cx<T>* tw) {
+  constexpr int LOG2L = ilog2c(L);
+  constexpr int NPASS = (LOG2L + 3) / 4;
+  constexpr int RL = 1 << (LOG2L - (NPASS - 1) * 4);
+  constexpr int R = (P + 1 == NPASS) ? RL : 16;
+  pass_compute<T, L, R, NS, INV>(v, j, tw);
+  if constexpr (P + 1 < NPASS) {
+    __syncthreads();  // everyone has finished reading the buffer
+    pass_store<T, L, R, NS>(v, buf, j);
+    __syncthreads();
+    pass_load<T, L>(v, buf, j);
+    fft_passes<T, L, INV, P + 1, NS * R>(v, buf, j, tw);
   }
 }
 
 // ------------------------------------------------------------------ the kernel
-template <typename T, int E, int MODE>
-__global__ void __launch_bounds__(512) line_pass_kernel(LinePassArgs<T> a, int npass, int rl,
-                                                        int line_stride) {
+template <typename T>
+struct MinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 2 : 1;
+};
+
+// Row c of U psi for U = [[c0 + i c3, c1 - i c2], [c1 + i c2, c0 - i c3]] stored as
+// u = (c0 - 1, c1, c2, c3): own = psi_c, oth = psi_(1-c).
+template <typename T>
+__device__ __forceinline__ Cx<T> apply_u_row(const Q4<T>& u, Cx<T> own, Cx<T> oth, int c) {
+  const T s3 = c ? -u.w : u.w, s2 = c ? u.z : -u.z;
+  // own + (c0-1) own + i s3 own + (c1 + i s2) oth
+  const T re = u.x * own.re - s3 * own.im + u.y * oth.re - s2 * oth.im;
+  const T im = u.x * own.im + s3 * own.re + u.y * oth.im + s2 * oth.re;
+  return {own.re + re, own.im + im};
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_pair(Cx<T> v) {
+  return {__shfl_xor_sync(0xffffffffu, v.re, 1), __shfl_xor_sync(0xffffffffu, v.im, 1)};
+}
+
+template <typename T, int L, int LPC, int MODE>
+__global__ void __launch_bounds__(Geo<T, L, LPC>::THREADS, MinBlocks<T>::value)
+    line_pass_kernel(LinePassArgs<T> a) {
+  using Gm = Geo<T, L, LPC>;
+  constexpr int J = Gm::J;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<T>* smem = reinterpret_cast<Cx<T>*>(smem_raw);
 
-  const int L = a.L;
-  const int tpl = L / E;                 // threads per line
   const int tid = threadIdx.x;
-  const int lcta = tid / tpl;            // line within the CTA
-  const int j = tid - lcta * tpl;
-  const int line = blockIdx.x * a.lpc + lcta;
-  const size_t row = (size_t)line * L;
+  const int lcta = tid / Gm::TPL;
+  const int r = tid - lcta * Gm::TPL;
+  const int c = r & 1;        // eigencomponent (step) or component (derivative)
+  const int j = r >> 1;
+  const size_t row = (size_t)(blockIdx.x * LPC + lcta) * L;
+  Cx<T>* buf = smem + lcta * Gm::STRIDE + c * Gm::COMP;
+  const T sg = c ? T(-1) : T(1);
+  // component c of point gi (the pair of threads reads one 2x8-B / 2x16-B point together)
+  const Cx<T>* in_c = reinterpret_cast<const Cx<T>*>(a.in) + c;
 
-  Cx<T>* b1 = smem + (size_t)lcta * line_stride;
-  Cx<T>* b2 = b1 + Pad<T>::len(L);
-
-  Cx<T> v1[E], v2[E];
-  // ---- load psi (both components) for elements j + m L/E
+  Cx<T> v[16];
+  // ---- load psi at j + m L/16 and form this thread's component
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const size_t gi = row + j + m * (L / E);
-    Q4<T> p = a.in[gi];
-    if (MODE == MODE_STEP && a.u_load) p = apply_u(a.u_load[gi], p);
-    v1[m] = {p.x, p.y};
-    v2[m] = {p.z, p.w};
-  }
-
-  line_fft<T, E, false>(v1, v2, b1, b2, j, L, npass, rl, a.tw);
-
-  // ---- k-space multiply at q = j + m L/E (the multiplier carries 1/L)
-#pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int q = j + m * (L / E);
-    const Q4<T> c = ldg_q4(a.mult + q);
-    const Cx<T> x1 = v1[m], x2 = v2[m];
-    if (MODE == MODE_DERIV) {
-      // i xi x, xi = c.z + c.w
-      v1[m] = {-(c.z * x1.im + c.w * x1.im), c.z * x1.re + c.w * x1.re};
-      v2[m] = {-(c.z * x2.im + c.w * x2.im), c.z * x2.re + c.w * x2.re};
-    } else if (a.sigma == 0) {
-      // (c-1) x - i s sigma_x x:  d1 = (c-1) x1 - i s x2,  d2 = (c-1) x2 - i s x1
-      v1[m] = {c.x * x1.re + (c.y * x1.re + (c.z * x2.im + c.w * x2.im)),
-               c.x * x1.im + (c.y * x1.im - (c.z * x2.re + c.w * x2.re))};
-      v2[m] = {c.x * x2.re + (c.y * x2.re + (c.z * x1.im + c.w * x1.im)),
-               c.x * x2.im + (c.y * x2.im - (c.z * x1.re + c.w * x1.re))};
+  for (int m = 0; m < 16; ++m) {
+    if ((m & 3) == 0) asm volatile("" ::: "memory");
+    const size_t gi = row + j + m * J;
+    Cx<T> own = in_c[2 * gi];
+    if constexpr (MODE == MODE_STEP) {
+      Cx<T> oth = shfl_pair(own);
+      if (a.u_load) {
+        const Q4<T> u = ldg_q4(a.u_load + gi);
+        own = apply_u_row(u, own, oth, c);
+        oth = shfl_pair(own);
+      }
+      const Cx<T> p1 = c ? oth : own, p2 = c ? own : oth;
+      if (a.sigma == 0) v[m] = {p1.re + sg * p2.re, p1.im + sg * p2.im};
+      else v[m] = {p1.re + sg * p2.im, p1.im - sg * p2.re};
     } else {
-      // (c-1) x - i s sigma_y x:  d1 = (c-1) x1 - s x2,  d2 = (c-1) x2 + s x1
-      v1[m] = {c.x * x1.re + (c.y * x1.re - (c.z * x2.re + c.w * x2.re)),
-               c.x * x1.im + (c.y * x1.im - (c.z * x2.im + c.w * x2.im))};
-      v2[m] = {c.x * x2.re + (c.y * x2.re + (c.z * x1.re + c.w * x1.re)),
-               c.x * x2.im + (c.y * x2.im + (c.z * x1.im + c.w * x1.im))};
+      v[m] = own;
     }
   }
 
-  line_fft<T, E, true>(v1, v2, b1, b2, j, L, npass, rl, a.tw);
+  fft_passes<T, L, false>(v, buf, j, a.tw);
 
-  // ---- epilogue into the staging buffer [lcta][i] (line stride L + 1 points)
-  __syncthreads();  // FFT buffers are free again
+  // ---- k-space multiply at q = j + m L/16 (the table carries the inverse FFT's scale)
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    if ((m & 3) == 0) asm volatile("" ::: "memory");
+    const Q4<T> q = ldg_q4(a.mult + j + m * J);
+    const T vr = v[m].re, vi = v[m].im;
+    if constexpr (MODE == MODE_DERIV) {
+      if constexpr (sizeof(T) == 4) {
+        v[m] = {-(q.z * vi + q.w * vi), q.z * vr + q.w * vr};
+      } else {
+        v[m] = {-q.z * vi, q.z * vr};
+      }
+    } else {
+      // eigenvalue +1 (c = 0): exp(-i th) - 1 = (cos - 1) - i sin; -1 (c = 1): + i sin
+      const T sh = -sg * q.z, sl = -sg * q.w;
+      if constexpr (sizeof(T) == 4) {
+        v[m] = {q.x * vr + ((q.y * vr - sl * vi) - sh * vi),
+                q.x * vi + ((q.y * vi + sl * vr) + sh * vr)};
+      } else {
+        v[m] = {q.x * vr - sh * vi, q.x * vi + sh * vr};
+      }
+    }
+  }
+
+  fft_passes<T, L, true>(v, buf, j, a.tw);
+
+  // ---- epilogue into the staging buffer [lcta][i] (line stride L + 1 points); thread c
+  // writes component c of each point
+  __syncthreads();  // the FFT buffers are free again
   Q4<T>* stage = reinterpret_cast<Q4<T>*>(smem_raw);
-  Q4<T>* my_stage = stage + (size_t)lcta * (L + 1);
+  Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
 #pragma unroll
-  for (int m = 0; m < E; ++m) {
-    const int i = j + m * (L / E);
-    Q4<T> o;
-    if (MODE == MODE_STEP) {
+  for (int m = 0; m < 16; ++m) {
+    if ((m & 3) == 0) asm volatile("" ::: "memory");
+    const int i = j + m * J;
+    if constexpr (MODE == MODE_STEP) {
       const size_t gi = row + i;
-      Q4<T> p = a.in[gi];
-      if (a.u_load) p = apply_u(a.u_load[gi], p);
+      // D_c from the two eigencomponents: sigma_x (D+ + D-, D+ - D-),
+      // sigma_y (D+ + D-, i (D+ - D-))
+      const Cx<T> oth = shfl_pair(v[m]);
+      const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
+      Cx<T> d;
+      if (c == 0) d = cadd(dp, dm);
+      else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+      Cx<T> p = in_c[2 * gi];
+      if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
       const T bm1 = a.beta ? a.beta[gi] : T(0);
-      o.x = (p.x + v1[m].re) + bm1 * v1[m].re;
-      o.y = (p.y + v1[m].im) + bm1 * v1[m].im;
-      o.z = (p.z + v2[m].re) + bm1 * v2[m].re;
-      o.w = (p.w + v2[m].im) + bm1 * v2[m].im;
-      if (a.u_store) o = apply_u(a.u_store[gi], o);
+      Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+      if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
+      my_stage[2 * i] = o;
     } else {
-      o = {v1[m].re, v1[m].im, v2[m].re, v2[m].im};
+      my_stage[2 * i] = v[m];
     }
-    my_stage[i] = o;
   }
 
-  // ---- transposed store: the cluster's G = lpc * cs lines go out as contiguous
-  // segments out[i][line0 .. line0 + G); CTA rank c writes rows i of its L/cs slice.
-  const int G = a.lpc * a.cs;
-  const int rank = (a.cs > 1) ? (int)cg::this_cluster().block_rank() : 0;
-  if (a.cs > 1) cg::this_cluster().sync(); else __syncthreads();
-  const int line0 = (blockIdx.x / a.cs) * G;
-  const int rows = L / a.cs;
-  const int i0 = rank * rows;
-  const int items = rows * G;
-  for (int it = tid; it < items; it += blockDim.x) {
-    const int g = it % G;
-    const int i = i0 + it / G;
-    const int owner = g / a.lpc;
-    const Q4<T>* src = stage;
-    if (a.cs > 1 && owner != rank) src = cg::this_cluster().map_shared_rank(stage, owner);
-    const Q4<T> val = src[(size_t)(g - owner * a.lpc) * (L + 1) + i];
-    a.out[(size_t)i * a.n_lines + line0 + g] = val;
+  // ---- transposed store: the cluster's GL lines go out as contiguous segments
+  // out[i][line0 .. line0 + GL); CTA rank q writes rows i of its L/CS slice. Remote
+  // (DSMEM) reads are issued in two rounds of four before the matching global stores.
+  constexpr int CS = Gm::CS, GL = Gm::GL, ROWS = L / CS;
+  int rank = 0;
+  if constexpr (CS > 1) {
+    rank = (int)cg::this_cluster().block_rank();
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
   }
-  if (a.cs > 1) cg::this_cluster().sync();
+  const int line0 = (blockIdx.x / CS) * GL;
+  const int i0 = rank * ROWS;
+  constexpr int HALF = Gm::NIT / 2;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    Q4<T> val[HALF];
+#pragma unroll
+    for (int q = 0; q < HALF; ++q) {
+      const int it = tid + (h * HALF + q) * Gm::THREADS;
+      const int g = it % GL;
+      const int i = i0 + it / GL;
+      const int owner = g / LPC;
+      const Q4<T>* src = stage;
+      if constexpr (CS > 1) {
+        if (owner != rank) src = cg::this_cluster().map_shared_rank(stage, owner);
+      }
+      val[q] = src[(size_t)(g - owner * LPC) * (L + 1) + i];
+    }
+#pragma unroll
+    for (int q = 0; q < HALF; ++q) {
+      const int it = tid + (h * HALF + q) * Gm::THREADS;
+      const int g = it % GL;
+      const int i = i0 + it / GL;
+      a.out[(size_t)i * a.n_lines + line0 + g] = val[q];
+    }
+  }
+  if constexpr (CS > 1) cg::this_cluster().sync();
 }
 
 }  // namespace dgb

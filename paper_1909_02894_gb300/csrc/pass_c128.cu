@@ -2,6 +2,5 @@
 #include "launch_impl.cuh"
 
 namespace dgb {
-template LaunchShape line_pass_shape<double>(int, int, int);
 template cudaError_t launch_line_pass<double>(const LinePassArgs<double>&, int, int, cudaStream_t);
 }  // namespace dgb

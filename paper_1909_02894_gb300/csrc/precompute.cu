@@ -197,8 +197,10 @@ cudaError_t launch_twiddles(int n, Cx<T>* tw, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Sec. 5: FFT index q -> p = q (q < n/2) or q - n, xi = p pi / a. The step multiplier is
-// exp(-i dt xi sigma) - I = (cos - 1) I - i sin sigma, scaled by the inverse FFT's 1/n.
+// Sec. 5: FFT index q -> p = q (q < n/2) or q - n, xi = p pi / a. In the eigenbasis of
+// sigma the step multiplier exp(-i dt xi sigma) - I has eigenvalues (cos - 1) -+ i sin;
+// the table holds (cos - 1, sin) scaled by 1/(2n): the inverse FFT's 1/n and the 1/2 of
+// the return from the (unnormalised) eigenbasis.
 template <typename T>
 __global__ void k_step_mult(int n, double a, double dt, Q4<T>* mult) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,8 +208,8 @@ __global__ void k_step_mult(int n, double a, double dt, Q4<T>* mult) {
   const int p = q < n / 2 ? q : q - n;
   const double th = dt * (p * (M_PI / a));
   const double hs = sin(0.5 * th);
-  const double cm1 = -2.0 * hs * hs / n;
-  const double sn = sin(th) / n;
+  const double cm1 = -hs * hs / n;
+  const double sn = 0.5 * sin(th) / n;
   Q4<T> r;
   split<T>(cm1, &r.x, &r.y);
   split<T>(sn, &r.z, &r.w);
