@@ -143,6 +143,26 @@ dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_
 /* Number of kernel launches this context has enqueued so far (for accounting). */
 long dirac_launch_count(const dirac_ctx *ctx);
 
+/* Norms of a device spinor without allocating device memory. The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc where they need a norm --
+ * code running during CUDA stream capture (allocation is not allowed there), services
+ * whose device memory all belongs to another allocator or a fixed arena, and loops that
+ * cannot afford cudaMalloc/cudaFree's implicit device synchronisation.
+ *   psi:    device [2][ny][nx] complex128 (the ABI spinor layout), read only
+ *   weight: device [ny][nx] doubles (e.g. w = sqrt(g11 g22 / g00)), or NULL for weight 1
+ *   out:    device pointer to 2 doubles, receives {hx hy sum |psi|^2, hx hy sum w |psi|^2}
+ *   cuda_stream: the stream to enqueue on (NULL = the default stream); nothing is
+ *   synchronised, out is valid once the stream reaches this point.
+ * Sizes: nx, ny powers of two in [16, 4096]; larger grids return DIRAC_EINVAL with a
+ * message in dirac_last_error(NULL). The partial sums live in a 32 KiB file-scope device
+ * array that every GPU loading the library holds until exit; the first call on a device
+ * looks up its device address (make that first call before any stream capture on that
+ * device). All calls share the array: calls that overlap on the GPU race, so order them
+ * on one stream or synchronise between them. Every call overwrites the partial sums it
+ * reads, so no clearing is needed. */
+dirac_status dirac_norms_noalloc(const double *psi, const double *weight, int nx, int ny,
+                                 double ax, double ay, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ DIRAC_CONN_COVARIANT, DIRAC_CONN_PAPER_2D, DIRAC_CONN_NONE = 0, 1, 2
 ABI_SYMBOLS = (
     "dirac_create", "dirac_set_state", "dirac_get_state", "dirac_step",
     "dirac_observables", "dirac_synchronize", "dirac_last_error", "dirac_destroy",
-    "dirac_set_launch", "dirac_launch_count",
+    "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc",
 )
 
 
@@ -93,6 +93,8 @@ def lib():
         L.dirac_set_launch.argtypes = [vp, i, i]
         L.dirac_launch_count.argtypes = [vp]
         L.dirac_launch_count.restype = l
+        L.dirac_norms_noalloc.argtypes = [vp, vp, i, i, d, d, vp, vp]
+        L.dirac_norms_noalloc.restype = C.c_int
         for f in ("dirac_create", "dirac_set_state", "dirac_get_state", "dirac_step",
                   "dirac_observables", "dirac_synchronize", "dirac_set_launch"):
             getattr(L, f).restype = C.c_int
@@ -189,6 +191,21 @@ def dirac_set_launch(ctx, threads_x: int, threads_y: int):
 
 def dirac_launch_count(ctx) -> int:
     return int(lib().dirac_launch_count(ctx))
+
+
+def dirac_norms_noalloc(psi, weight, ax: float, ay: float, out, stream=None):
+    """Norms of a CUDA complex128 [2][ny][nx] tensor without device allocation: writes
+    {norm, weighted norm} into out (a CUDA float64 tensor of 2). weight: CUDA float64
+    [ny][nx] tensor or None. Enqueued on `stream` (a raw handle; None = default stream)."""
+    assert psi.is_cuda and psi.is_contiguous() and str(psi.dtype) == "torch.complex128"
+    assert out.is_cuda and str(out.dtype) == "torch.float64" and out.numel() >= 2
+    ny, nx = int(psi.shape[-2]), int(psi.shape[-1])
+    wp = None
+    if weight is not None:
+        assert weight.is_cuda and weight.is_contiguous() and str(weight.dtype) == "torch.float64"
+        wp = weight.data_ptr()
+    _check(lib().dirac_norms_noalloc(psi.data_ptr(), wp, nx, ny, float(ax), float(ay),
+                                     out.data_ptr(), stream), None)
 
 
 def dirac_destroy(ctx):

@@ -50,6 +50,10 @@ struct dirac_ctx {
 
 static thread_local std::string g_create_error;
 
+namespace dgb {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace dgb
+
 static size_t npts(const dirac_ctx* c) { return (size_t)c->nx * c->ny; }
 
 static dirac_status fail(dirac_ctx* c, dirac_status s, const std::string& msg) {

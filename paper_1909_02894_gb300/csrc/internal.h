@@ -10,6 +10,9 @@
 
 namespace dgb {
 
+// Sets the text that dirac_last_error(NULL) returns (errors without a context).
+void set_global_error(const std::string& msg);
+
 // Enqueues one fused line pass (MODE_STEP or MODE_DERIV). opt selects the CTA shape:
 // 0 = about 256 threads per CTA, 1 = 512 threads (step mode only).
 template <typename T>
