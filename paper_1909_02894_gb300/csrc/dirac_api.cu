@@ -260,8 +260,8 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
     CK(cudaMallocAsync(&ty, ny * sizeof(Cx<double>), st), "allocate");
     CK(cudaMallocAsync(&mx, nx * sizeof(Q4<double>), st), "allocate");
     CK(cudaMallocAsync(&my, ny * sizeof(Q4<double>), st), "allocate");
-    CK(launch_twiddles<double>(nx, (Cx<double>*)tx, st), "twiddles");
-    CK(launch_twiddles<double>(ny, (Cx<double>*)ty, st), "twiddles");
+    CK(launch_twiddles<double>(nx, line_pass_radix<double>(nx), (Cx<double>*)tx, st), "twiddles");
+    CK(launch_twiddles<double>(ny, line_pass_radix<double>(ny), (Cx<double>*)ty, st), "twiddles");
     CK(launch_deriv_mult<double>(nx, ctx->ax, (Q4<double>*)mx, st), "derivative table");
     CK(launch_deriv_mult<double>(ny, ctx->ay, (Q4<double>*)my, st), "derivative table");
     LinePassArgs<double> d{};
@@ -291,8 +291,8 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
   CK(launch_beta<T>(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, nx, ny, (T*)ctx->beta1,
                     (T*)ctx->beta2T, st),
      "b - 1");
-  CK(launch_twiddles<T>(nx, (Cx<T>*)ctx->tw_x, st), "twiddles");
-  CK(launch_twiddles<T>(ny, (Cx<T>*)ctx->tw_y, st), "twiddles");
+  CK(launch_twiddles<T>(nx, line_pass_radix<T>(nx), (Cx<T>*)ctx->tw_x, st), "twiddles");
+  CK(launch_twiddles<T>(ny, line_pass_radix<T>(ny), (Cx<T>*)ctx->tw_y, st), "twiddles");
   CK(launch_deriv_mult<T>(nx, ctx->ax, (Q4<T>*)ctx->dmult_x, st), "derivative table");
   CK(launch_deriv_mult<T>(ny, ctx->ay, (Q4<T>*)ctx->dmult_y, st), "derivative table");
   ctx->launches += 7;

@@ -17,6 +17,10 @@ void set_global_error(const std::string& msg);
 // 0 = about 256 threads per CTA, 1 = 512 threads (step mode only).
 template <typename T>
 cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st);
+// Elements per thread (8 or 16) the line pass uses for line length L; the twiddle table
+// of that axis must be built for the same value.
+template <typename T>
+int line_pass_radix(int L);
 
 // ---- FP64 precompute (precompute.cu)
 // a1, a2, meff, w and the two log fields (packed as a complex128 spinor (f1, f2)) from the
@@ -43,10 +47,10 @@ template <typename T>
 cudaError_t launch_halfstep(const double* a1, const double* a2, const double* meff,
                             const double* omx, const double* omy, int nx, int ny, double dt,
                             Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, cudaStream_t st);
-// Per-axis tables: twiddles exp(-2 pi i m / n); step multipliers
+// Per-axis tables: per-pass twiddle blocks (layout in line_pass.cuh); step multipliers
 // ((cos(dt xi) - 1)/n, sin(dt xi)/n) as hi/lo pairs; derivative multipliers xi/n.
 template <typename T>
-cudaError_t launch_twiddles(int n, Cx<T>* tw, cudaStream_t st);
+cudaError_t launch_twiddles(int n, int e, Cx<T>* tw, cudaStream_t st);
 template <typename T>
 cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream_t st);
 template <typename T>

@@ -6,11 +6,18 @@
 
 namespace dgb {
 
+// Elements per thread: FP32 lines of 256 points or more use E = 8 (radix-8 passes; the
+// FFT state of a thread fits the 64-register budget of 1024 threads per SM without
+// spilling); shorter lines and FP64 use E = 16.
+template <typename T>
+constexpr int radix_e(int L) { return (sizeof(T) == 4 && L >= 256) ? 8 : 16; }
+
 template <typename T, int L, int LPC, int MODE>
 static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
-  using Gm = Geo<T, L, LPC>;
+  constexpr int E = radix_e<T>(L);
+  using Gm = Geo<T, L, LPC, E>;
   if (a.n_lines % Gm::GL != 0 || a.n_lines < Gm::GL) return cudaErrorInvalidValue;
-  auto kern = line_pass_kernel<T, L, LPC, MODE>;
+  auto kern = line_pass_kernel<T, L, LPC, E, MODE>;
   // Function attributes are per device; set them once per device for this kernel.
   static bool configured[64] = {false};
   int dev = 0;
@@ -42,11 +49,15 @@ static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-// Two CTA shapes per line length: opt 0 (about 256 threads) and opt 1 (512 threads);
-// lines of 128 points or fewer use 16 lines per CTA, 4096-point lines one line of 512
-// threads.
+// Two CTA shapes per line length (opt 0 smaller, opt 1 larger; lines of 128 points or
+// fewer and 4096-point lines have one). Lines per CTA, by precision:
+//   FP32 (E = 8 from 256 points): 256: 4|8, 512: 2|4, 1024: 1|2, 2048: 1|2, 4096: 1
+//     (256|512 threads, 512|1024 at 2048, 1024 at 4096)
+//   FP64 (E = 16): 256: 8|16, 512: 4|8, 1024: 2|4, 2048: 1|2, 4096: 1 (256|512 threads)
+//   both: 16 lines per CTA up to 128 points.
 template <typename T, int MODE>
 static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) {
+  constexpr bool F = sizeof(T) == 4;
   const bool big = (MODE == MODE_STEP) && opt != 0;
   switch (a.L) {
     case 16: return launch_one<T, 16, 16, MODE>(a, st);
@@ -59,18 +70,18 @@ static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) 
   if constexpr (MODE == MODE_STEP) {
     if (big) {
       switch (a.L) {
-        case 256: return launch_one<T, 256, 16, MODE>(a, st);
-        case 512: return launch_one<T, 512, 8, MODE>(a, st);
-        case 1024: return launch_one<T, 1024, 4, MODE>(a, st);
+        case 256: return launch_one<T, 256, F ? 8 : 16, MODE>(a, st);
+        case 512: return launch_one<T, 512, F ? 4 : 8, MODE>(a, st);
+        case 1024: return launch_one<T, 1024, F ? 2 : 4, MODE>(a, st);
         case 2048: return launch_one<T, 2048, 2, MODE>(a, st);
         default: return cudaErrorInvalidValue;
       }
     }
   }
   switch (a.L) {
-    case 256: return launch_one<T, 256, 8, MODE>(a, st);
-    case 512: return launch_one<T, 512, 4, MODE>(a, st);
-    case 1024: return launch_one<T, 1024, 2, MODE>(a, st);
+    case 256: return launch_one<T, 256, F ? 4 : 8, MODE>(a, st);
+    case 512: return launch_one<T, 512, F ? 2 : 4, MODE>(a, st);
+    case 1024: return launch_one<T, 1024, F ? 1 : 2, MODE>(a, st);
     case 2048: return launch_one<T, 2048, 1, MODE>(a, st);
     default: return cudaErrorInvalidValue;
   }
@@ -81,5 +92,8 @@ cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaSt
   if (mode == MODE_DERIV) return dispatch<T, MODE_DERIV>(a, 0, st);
   return dispatch<T, MODE_STEP>(a, opt, st);
 }
+
+template <typename T>
+int line_pass_radix(int L) { return radix_e<T>(L); }
 
 }  // namespace dgb

@@ -17,11 +17,12 @@
 // as a deviation from identity keeps FP32 rounding proportional to |exp(..) - 1|.
 // Derivative mode (Sec. 5 eq. trick): out_c = F^-1[ i xi / L  F psi_c ] per component.
 //
-// FFT: radix-16 Stockham autosort. Thread (j, c) of a line holds elements j + m L/16
-// (m < 16) of component c; that index set is the input of the first pass and the output
-// of the last one for any radix sequence, so the global load, the k-space multiply and
-// the epilogue happen in registers and only the passes in between go through shared
-// memory. The line length L is a template parameter: all index arithmetic folds.
+// FFT: radix-E Stockham autosort (E = 8 or 16 elements per thread). Thread (j, c) of a
+// line holds elements j + m L/E (m < E) of component c; that index set is the input of
+// the first pass and the output of the last one for any radix sequence, so the global
+// load, the k-space multiply and the epilogue happen in registers and only the passes in
+// between go through shared memory. L and E are template parameters: all index
+// arithmetic folds.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -40,7 +41,7 @@ struct LinePassArgs {
   int L;                // line length = FFT size (power of two, 16..4096)
   int n_lines;          // lines in the input = row length of the output
   int sigma;            // 0: sigma_x (x pass), 1: sigma_y (y pass)
-  const Cx<T>* tw;      // tw[m] = exp(-2 pi i m / L), m < L
+  const Cx<T>* tw;      // per-pass twiddles, see tw_offset (at most L entries)
   const Q4<T>* mult;    // per k index q: step ((cos - 1) hi, lo, sin hi, lo) / (2L);
                         // derivative (0, 0, xi hi, xi lo) / L
   const T* beta;        // b - 1 per input point, or nullptr (b = 1)
@@ -115,9 +116,9 @@ __device__ __forceinline__ void dft8(Cx<T> (&x)[8]) {
   x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
 }
 
-// Radix-16 butterfly with an optional input twiddle W^(t step) on element t (t >= 1),
-// loaded from the table just before the inner DFT4 that consumes it, so that only four
-// twiddles are live at a time.
+// Radix-16 butterfly with an optional input twiddle tw[(t - 1) step] on element t
+// (t >= 1; tw points at the thread's k within its pass block and step = NS), loaded just
+// before the inner DFT4 that consumes it so that only four twiddles are live at a time.
 template <typename T, bool INV, bool TW>
 __device__ __forceinline__ void dft16(Cx<T> (&x)[16], const Cx<T>* __restrict__ tw = nullptr,
                                       int step = 0) {
@@ -129,7 +130,7 @@ __device__ __forceinline__ void dft16(Cx<T> (&x)[16], const Cx<T>* __restrict__ 
       for (int n1 = 0; n1 < 4; ++n1) {
         const int t = 4 * n1 + n2;
         if (t == 0) continue;
-        const Cx<T> w = ldg_cx(tw + t * step);
+        const Cx<T> w = ldg_cx(tw + (t - 1) * step);
         x[t] = INV ? cmulc(x[t], w) : cmul(x[t], w);
       }
       asm volatile("" ::: "memory");
@@ -173,49 +174,72 @@ __device__ __forceinline__ void dftR(Cx<T> (&x)[R]) {
 // ------------------------------------------------------------- geometry
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
-// Compile-time launch geometry for line length L and LPC lines per CTA.
-// Shared memory per line: two components of P = L + L/16 padded slots (one pad slot per
-// 16 keeps the strided Stockham writes conflict-free), the second component offset by
-// half a 128-B bank row so that the two threads of a point pair never collide, plus a
-// small line pad for short lines. A CPU model of every access pattern (all L, both
-// precisions, 128..512 threads) finds no bank conflicts with these offsets.
-template <typename T, int L_, int LPC_>
+// Twiddle table layout: the passes after the first (span NS = E, E^2, ...) each own a
+// block [(t - 1) NS + k] = exp(-2 pi i t k / (NS R)), t = 1..R-1, k < NS, so that the
+// lanes of a warp (consecutive k) read consecutive entries. Every pass but the last has
+// radix E; the block of span NS starts after the (E - 1) NS' entries of each earlier span.
+__host__ __device__ constexpr int tw_offset(int NS, int E) {
+  return NS <= E ? 0 : tw_offset(NS / E, E) + (E - 1) * (NS / E);
+}
+
+// Compile-time launch geometry for line length L, LPC lines per CTA and E elements per
+// thread. Shared memory per line: two components of P = L + L/E padded slots (one pad slot
+// per E keeps the strided Stockham writes conflict-free), the second component offset by
+// half a 128-B bank row (a few short lines take other offsets) so that the two threads of
+// a point pair never collide, plus a small line pad for short lines. A CPU model of every
+// access pattern (all L, both precisions, E = 8 and 16, 256..1024 threads) finds no bank
+// conflicts with these offsets.
+template <typename T, int L, int E>
+struct SmemPlan {
+  static constexpr int B = sizeof(T) == 4 ? 16 : 8;  // slots per 128 B
+  static constexpr bool F = sizeof(T) == 4;
+  static constexpr int CM = (E == 16) ? ((!F && L == 32) ? 2 : B / 2)
+                                      : ((L == 16) ? 2 : (F && L == 32) ? 4 : B / 2);
+  static constexpr int EXTRA = (E == 16 && F && L == 32) ? 2 : (E == 16 && F && L == 64) ? 4 : 0;
+};
+
+template <typename T, int L_, int LPC_, int E_>
 struct Geo {
   static constexpr int L = L_;
   static constexpr int LPC = LPC_;
-  static constexpr int E = 16;                  // elements per thread
+  static constexpr int E = E_;                  // elements per thread
+  static constexpr int SH = ilog2c(E);          // pad one slot every E slots
   static constexpr int J = L / E;               // index groups per line
   static constexpr int TPL = 2 * J;             // threads per line (two components)
   static constexpr int THREADS = LPC * TPL;
-  static constexpr int B = sizeof(T) == 4 ? 16 : 8;   // slots per 128 B
-  static constexpr int P = L + L / 16;
-  static constexpr int CM = (sizeof(T) == 8 && L == 32) ? 2 : B / 2;
+  static constexpr int B = SmemPlan<T, L, E>::B;
+  static constexpr int P = L + L / E;
+  static constexpr int CM = SmemPlan<T, L, E>::CM;
   static constexpr int COMP = P + (((CM - P % B) % B) + B) % B;
-  static constexpr int EXTRA = (sizeof(T) == 4 && L == 32) ? 2 : (sizeof(T) == 4 && L == 64) ? 4 : 0;
-  static constexpr int STRIDE = 2 * COMP + EXTRA;
-  static constexpr int G = sizeof(T) == 4 ? 8 : 4;    // lines per 128-B output segment
+  static constexpr int STRIDE = 2 * COMP + SmemPlan<T, L, E>::EXTRA;
+  // Lines gathered per output segment: 4 (64 B complex64, 128 B complex128). A cluster of
+  // 4 CTAs packs the GPCs better than 8 and measured faster at 1024..4096 points.
+  static constexpr int G = 4;
   static constexpr int CS = LPC >= G ? 1 : G / LPC;   // CTAs per cluster
   static constexpr int GL = LPC * CS;                  // lines gathered per output segment
   static constexpr int LOG2L = ilog2c(L);
-  static constexpr int NPASS = (LOG2L + 3) / 4;
-  static constexpr int RL = 1 << (LOG2L - (NPASS - 1) * 4);
+  static constexpr int NPASS = (LOG2L + SH - 1) / SH;
+  static constexpr int RL = 1 << (LOG2L - (NPASS - 1) * SH);
   static constexpr size_t FFT_BYTES = (size_t)LPC * STRIDE * sizeof(Cx<T>);
   static constexpr size_t STAGE_BYTES = (size_t)LPC * (L + 1) * sizeof(Q4<T>);
   static constexpr size_t SMEM = FFT_BYTES > STAGE_BYTES ? FFT_BYTES : STAGE_BYTES;
   static constexpr int NIT = (L / CS) * GL / THREADS;  // transposed-store items per thread
   static_assert((L & (L - 1)) == 0 && L >= 16, "L must be a power of two >= 16");
-  static_assert(THREADS <= 512, "at most 512 threads per CTA");
-  static_assert((L / CS) * GL == NIT * THREADS, "store items must divide evenly");
+  static_assert(E == 8 || E == 16, "E must be 8 or 16");
+  static_assert(THREADS <= 1024, "at most 1024 threads per CTA");
+  static_assert((L / CS) * GL == NIT * THREADS && NIT % 2 == 0, "store items must divide");
 };
 
-__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+template <int E>
+__device__ __forceinline__ int spad(int i) { return i + (i >> ilog2c(E)); }
 
 // ------------------------------------------------------------- Stockham passes
-// Butterfly u (u < 16/R) works on index s = j + u L/16 and elements v[u + t 16/R]
-// (t < R): twiddle by W_{NS R}^{t k} with k = s mod NS, then the R-point DFT.
-template <typename T, int L, int R, int NS, bool INV>
-__device__ __forceinline__ void pass_compute(Cx<T> (&v)[16], int j, const Cx<T>* __restrict__ tw) {
-  constexpr int NB = 16 / R, J = L / 16;
+// Butterfly u (u < E/R) works on index s = j + u L/E and elements v[u + t E/R]
+// (t < R): twiddle by W_{NS R}^{t k} with k = s mod NS (from the pass's table block),
+// then the R-point DFT.
+template <typename T, int L, int E, int R, int NS, bool INV>
+__device__ __forceinline__ void pass_compute(Cx<T> (&v)[E], int j, const Cx<T>* __restrict__ tw) {
+  constexpr int NB = E / R, J = L / E;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
     Cx<T> x[R];
@@ -223,14 +247,14 @@ __device__ __forceinline__ void pass_compute(Cx<T> (&v)[16], int j, const Cx<T>*
     for (int t = 0; t < R; ++t) x[t] = v[u + t * NB];
     if constexpr (NS > 1 && R == 16) {
       const int k = (j + u * J) & (NS - 1);
-      dft16<T, INV, true>(x, tw, k * (L / (NS * R)));
+      dft16<T, INV, true>(x, tw + tw_offset(NS, E) + k, NS);
     } else {
       if constexpr (NS > 1) {
         const int k = (j + u * J) & (NS - 1);
-        const int step = k * (L / (NS * R));
+        const Cx<T>* twk = tw + tw_offset(NS, E) + k;
 #pragma unroll
         for (int t = 1; t < R; ++t) {
-          const Cx<T> w = ldg_cx(tw + t * step);
+          const Cx<T> w = ldg_cx(twk + (t - 1) * NS);
           x[t] = INV ? cmulc(x[t], w) : cmul(x[t], w);
         }
       }
@@ -242,57 +266,62 @@ __device__ __forceinline__ void pass_compute(Cx<T> (&v)[16], int j, const Cx<T>*
 }
 
 // Output (u, t) of a pass goes to index (s - k) R + k + t NS (padded).
-template <typename T, int L, int R, int NS>
-__device__ __forceinline__ void pass_store(const Cx<T> (&v)[16], Cx<T>* buf, int j) {
-  constexpr int NB = 16 / R, J = L / 16;
+template <typename T, int L, int E, int R, int NS>
+__device__ __forceinline__ void pass_store(const Cx<T> (&v)[E], Cx<T>* buf, int j) {
+  constexpr int NB = E / R, J = L / E;
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
     const int s = j + u * J;
     const int k = s & (NS - 1);
-    const int base = spad((s - k) * R + k);
+    const int base = spad<E>((s - k) * R + k);
 #pragma unroll
     for (int t = 0; t < R; ++t) {
-      // NS = 1 only in the first pass, which is radix 16, so base is a multiple of 17
-      // there; otherwise NS is a multiple of 16 and each step adds NS + NS/16 slots.
-      const int o = (NS == 1) ? base + t : base + t * (NS + NS / 16);
+      // NS = 1 only in the first pass (radix E, base a multiple of E + 1 slots); there the
+      // t-th output is the next slot. NS a multiple of E adds NS + NS/E slots per step.
+      const int o = (NS == 1) ? base + t : base + t * (NS + NS / E);
       buf[o] = v[u + t * NB];
     }
   }
 }
 
-template <typename T, int L>
-__device__ __forceinline__ void pass_load(Cx<T> (&v)[16], const Cx<T>* buf, int j) {
-  constexpr int J = L / 16;
-  if constexpr (J % 16 == 0) {
-    const int b = spad(j);
+template <typename T, int L, int E>
+__device__ __forceinline__ void pass_load(Cx<T> (&v)[E], const Cx<T>* buf, int j) {
+  constexpr int J = L / E;
+  if constexpr (J % E == 0) {
+    const int b = spad<E>(j);
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = buf[b + m * (J + J / 16)];
+    for (int m = 0; m < E; ++m) v[m] = buf[b + m * (J + J / E)];
   } else {
 #pragma unroll
-    for (int m = 0; m < 16; ++m) v[m] = buf[spad(j + m * J)];
+    for (int m = 0; m < E; ++m) v[m] = buf[spad<E>(j + m * J)];
   }
 }
 
-template <typename T, int L, bool INV, int P = 0, int NS = 1>
-__device__ __forceinline__ void fft_passes(Cx<T> (&v)[16], Cx<T>* buf, int j, const Cx<T>* tw) {
+template <typename T, int L, int E, bool INV, int P = 0, int NS = 1>
+__device__ __forceinline__ void fft_passes(Cx<T> (&v)[E], Cx<T>* buf, int j, const Cx<T>* tw) {
+  constexpr int SH = ilog2c(E);
   constexpr int LOG2L = ilog2c(L);
-  constexpr int NPASS = (LOG2L + 3) / 4;
-  constexpr int RL = 1 << (LOG2L - (NPASS - 1) * 4);
-  constexpr int R = (P + 1 == NPASS) ? RL : 16;
-  pass_compute<T, L, R, NS, INV>(v, j, tw);
+  constexpr int NPASS = (LOG2L + SH - 1) / SH;
+  constexpr int RL = 1 << (LOG2L - (NPASS - 1) * SH);
+  constexpr int R = (P + 1 == NPASS) ? RL : E;
+  pass_compute<T, L, E, R, NS, INV>(v, j, tw);
   if constexpr (P + 1 < NPASS) {
     __syncthreads();  // everyone has finished reading the buffer
-    pass_store<T, L, R, NS>(v, buf, j);
+    pass_store<T, L, E, R, NS>(v, buf, j);
     __syncthreads();
-    pass_load<T, L>(v, buf, j);
-    fft_passes<T, L, INV, P + 1, NS * R>(v, buf, j, tw);
+    pass_load<T, L, E>(v, buf, j);
+    fft_passes<T, L, E, INV, P + 1, NS * R>(v, buf, j, tw);
   }
 }
 
 // ------------------------------------------------------------------ the kernel
-template <typename T>
+// Occupancy target: FP32 radix-8 CTAs fill 1024 threads per SM at <= 64 registers (the
+// E = 8 state fits without spilling); FP32 radix-16 CTAs 512 threads per SM at <= 128
+// registers; FP64 CTAs take up to 128 registers (the FP64 path is ALU bound).
+template <typename T, int THREADS, int E>
 struct MinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int want = sizeof(T) == 4 ? (E == 8 ? 1024 : 512) / THREADS : 1;
+  static constexpr int value = want < 1 ? 1 : want;
 };
 
 // Row c of U psi for U = [[c0 + i c3, c1 - i c2], [c1 + i c2, c0 - i c3]] stored as
@@ -311,10 +340,11 @@ __device__ __forceinline__ Cx<T> shfl_pair(Cx<T> v) {
   return {__shfl_xor_sync(0xffffffffu, v.re, 1), __shfl_xor_sync(0xffffffffu, v.im, 1)};
 }
 
-template <typename T, int L, int LPC, int MODE>
-__global__ void __launch_bounds__(Geo<T, L, LPC>::THREADS, MinBlocks<T>::value)
+template <typename T, int L, int LPC, int E, int MODE>
+__global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
+                                  MinBlocks<T, Geo<T, L, LPC, E>::THREADS, E>::value)
     line_pass_kernel(LinePassArgs<T> a) {
-  using Gm = Geo<T, L, LPC>;
+  using Gm = Geo<T, L, LPC, E>;
   constexpr int J = Gm::J;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<T>* smem = reinterpret_cast<Cx<T>*>(smem_raw);
@@ -330,10 +360,10 @@ __global__ void __launch_bounds__(Geo<T, L, LPC>::THREADS, MinBlocks<T>::value)
   // component c of point gi (the pair of threads reads one 2x8-B / 2x16-B point together)
   const Cx<T>* in_c = reinterpret_cast<const Cx<T>*>(a.in) + c;
 
-  Cx<T> v[16];
-  // ---- load psi at j + m L/16 and form this thread's component
+  Cx<T> v[E];
+  // ---- load psi at j + m L/E and form this thread's component
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < E; ++m) {
     if ((m & 3) == 0) asm volatile("" ::: "memory");
     const size_t gi = row + j + m * J;
     Cx<T> own = in_c[2 * gi];
@@ -352,11 +382,11 @@ __global__ void __launch_bounds__(Geo<T, L, LPC>::THREADS, MinBlocks<T>::value)
     }
   }
 
-  fft_passes<T, L, false>(v, buf, j, a.tw);
+  fft_passes<T, L, E, false>(v, buf, j, a.tw);
 
-  // ---- k-space multiply at q = j + m L/16 (the table carries the inverse FFT's scale)
+  // ---- k-space multiply at q = j + m L/E (the table carries the inverse FFT's scale)
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < E; ++m) {
     if ((m & 3) == 0) asm volatile("" ::: "memory");
     const Q4<T> q = ldg_q4(a.mult + j + m * J);
     const T vr = v[m].re, vi = v[m].im;
@@ -378,7 +408,7 @@ __global__ void __launch_bounds__(Geo<T, L, LPC>::THREADS, MinBlocks<T>::value)
     }
   }
 
-  fft_passes<T, L, true>(v, buf, j, a.tw);
+  fft_passes<T, L, E, true>(v, buf, j, a.tw);
 
   // ---- epilogue into the staging buffer [lcta][i] (line stride L + 1 points); thread c
   // writes component c of each point
@@ -386,7 +416,7 @@ __global__ void __launch_bounds__(Geo<T, L, LPC>::THREADS, MinBlocks<T>::value)
   Q4<T>* stage = reinterpret_cast<Q4<T>*>(smem_raw);
   Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
 #pragma unroll
-  for (int m = 0; m < 16; ++m) {
+  for (int m = 0; m < E; ++m) {
     if ((m & 3) == 0) asm volatile("" ::: "memory");
     const int i = j + m * J;
     if constexpr (MODE == MODE_STEP) {

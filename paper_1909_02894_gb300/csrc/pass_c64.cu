@@ -3,4 +3,5 @@
 
 namespace dgb {
 template cudaError_t launch_line_pass<float>(const LinePassArgs<float>&, int, int, cudaStream_t);
+template int line_pass_radix<float>(int);
 }  // namespace dgb

@@ -182,18 +182,37 @@ __device__ inline void split(double v, T* hi, T* lo) {
   *lo = (T)(v - (double)h);
 }
 
+// Per-pass twiddle blocks (layout in line_pass.cuh, tw_offset) for E elements per
+// thread: for every pass after the first, span NS (E, E^2, ...) and radix R (E, or the
+// remaining radix for the last pass), entries [(t - 1) NS + k] = exp(-2 pi i t k/(NS R)).
+// Computed in FP64.
 template <typename T>
-__global__ void k_twiddles(int n, Cx<T>* tw) {
+__global__ void k_twiddles(int n, int e, Cx<T>* tw) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
-  double s, c;
-  sincospi(2.0 * m / n, &s, &c);
-  tw[m] = {(T)c, (T)(-s)};
+  int log2n = 0, log2e = 0;
+  while ((1 << log2n) < n) ++log2n;
+  while ((1 << log2e) < e) ++log2e;
+  const int npass = (log2n + log2e - 1) / log2e;
+  int off = 0, ns = e;
+  for (int p = 1; p < npass; ++p, ns *= e) {
+    const int r = (p + 1 == npass) ? (1 << (log2n - (npass - 1) * log2e)) : e;
+    const int cnt = (r - 1) * ns;
+    if (m < off + cnt) {
+      const int t = (m - off) / ns + 1, k = (m - off) % ns;
+      double s, c;
+      sincospi(2.0 * (double)t * k / ((double)ns * r), &s, &c);
+      tw[m] = {(T)c, (T)(-s)};
+      return;
+    }
+    off += cnt;
+  }
+  tw[m] = {(T)1, (T)0};  // unused entries
 }
 
 template <typename T>
-cudaError_t launch_twiddles(int n, Cx<T>* tw, cudaStream_t st) {
-  k_twiddles<T><<<nblocks(n), TPB, 0, st>>>(n, tw);
+cudaError_t launch_twiddles(int n, int e, Cx<T>* tw, cudaStream_t st) {
+  k_twiddles<T><<<nblocks(n), TPB, 0, st>>>(n, e, tw);
   return cudaGetLastError();
 }
 
@@ -268,7 +287,7 @@ cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cu
   template cudaError_t launch_halfstep<T>(const double*, const double*, const double*,      \
                                           const double*, const double*, int, int, double,    \
                                           Q4<T>*, Q4<T>*, Q4<T>*, cudaStream_t);             \
-  template cudaError_t launch_twiddles<T>(int, Cx<T>*, cudaStream_t);                         \
+  template cudaError_t launch_twiddles<T>(int, int, Cx<T>*, cudaStream_t);                    \
   template cudaError_t launch_step_mult<T>(int, double, double, Q4<T>*, cudaStream_t);        \
   template cudaError_t launch_deriv_mult<T>(int, double, Q4<T>*, cudaStream_t);               \
   template cudaError_t launch_transpose<T>(const Q4<T>*, Q4<T>*, int, int, cudaStream_t);
