@@ -124,7 +124,10 @@ dirac_status dirac_step(dirac_ctx *ctx, long n_steps, double dt);
  * (after filling *out) if the norm is not finite. */
 dirac_status dirac_observables(dirac_ctx *ctx, dirac_obs *out, double *density_or_NULL);
 
-/* Blocks until all work enqueued on the context's stream has finished. */
+/* Blocks until all work enqueued on the context's stream has finished. Returns
+ * DIRAC_ETIMEOUT if a bounded wait inside a kernel ran out since the last check (the
+ * state is then not valid); dirac_get_state to the host and dirac_observables check the
+ * same flag. */
 dirac_status dirac_synchronize(dirac_ctx *ctx);
 
 /* Text of the last error on ctx (or of the last failed dirac_create when ctx is NULL).
@@ -136,8 +139,11 @@ void dirac_destroy(dirac_ctx *ctx);
 
 /* CTA shape of the two fused passes (each pass: FFT along a line, k-space multiply,
  * inverse FFT, combine, transposed store): about 256 or 512 threads per CTA for that
- * pass's line length; 0 = the default (512). Lines of 128 points or fewer and 4096-point
- * lines have one shape only. Used by the autotuner. DIRAC_EINVAL for other values. */
+ * pass's line length, or 1024 for the persistent prefetching variant (complex64, lines
+ * of 256..4096 points; one CTA per SM streams the next lines into shared memory while
+ * it transforms the current ones); 0 = the default (persistent for complex64 lines of
+ * 1024 points or more, else 512). Lines of 128 points or fewer have one shape only.
+ * Used by the autotuner. DIRAC_EINVAL for other values. */
 dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_pass);
 
 /* Number of kernel launches this context has enqueued so far (for accounting). */

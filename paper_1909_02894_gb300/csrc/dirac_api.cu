@@ -40,6 +40,7 @@ struct dirac_ctx {
   void *scratch1 = nullptr, *scratch2 = nullptr;
   double *partials = nullptr, *result = nullptr, *density = nullptr;
 
+  int* d_err = nullptr;       // device error flag written by bounded waits
   double dt_cached = 0.0;
   bool state_set = false;
   int threads_x = 0, threads_y = 0;
@@ -87,9 +88,31 @@ static void free_all(dirac_ctx* ctx) {
 }
 
 // ------------------------------------------------------------------ precision dispatch
+// launch option for a pass from the dirac_set_launch preference (0 = default)
+static int pass_opt(const dirac_ctx* ctx, int threads, int L) {
+  if (threads == 256) return 0;
+  if (threads == 512) return 1;
+  if (threads == 1024) return 2;
+  // default: the persistent prefetching pass for long complex64 lines
+  return (ctx->prec == DIRAC_C64 && L >= 1024) ? 2 : 1;
+}
+
+// Reads and clears the device error flag (after the stream has been synchronised).
+static dirac_status device_error(dirac_ctx* ctx) {
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
+  if (flag) {
+    cudaMemset(ctx->d_err, 0, sizeof(int));
+    return fail(ctx, DIRAC_ETIMEOUT, "a bounded device wait ran out; the state is not valid");
+  }
+  return DIRAC_OK;
+}
+
 template <typename T>
 static LinePassArgs<T> pass_args(dirac_ctx* ctx, int axis) {
   LinePassArgs<T> a{};
+  a.err = ctx->d_err;
   a.L = axis == 0 ? ctx->nx : ctx->ny;
   a.n_lines = axis == 0 ? ctx->ny : ctx->nx;
   a.sigma = axis;
@@ -131,11 +154,13 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   for (long s = 0; s < n; ++s) {
     ax.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
     ax.u_store = nullptr;
-    CK(launch_line_pass<T>(ax, MODE_STEP, ctx->threads_x == 256 ? 0 : 1, ctx->stream), "x pass");
+    CK(launch_line_pass<T>(ax, MODE_STEP, pass_opt(ctx, ctx->threads_x, ctx->nx), ctx->stream),
+       "x pass");
     ay.u_load = nullptr;
     ay.u_store = ctx->u_identity ? nullptr
                                  : (const Q4<T>*)(s + 1 == n ? ctx->u_t : ctx->u2_t);
-    CK(launch_line_pass<T>(ay, MODE_STEP, ctx->threads_y == 256 ? 0 : 1, ctx->stream), "y pass");
+    CK(launch_line_pass<T>(ay, MODE_STEP, pass_opt(ctx, ctx->threads_y, ctx->ny), ctx->stream),
+       "y pass");
     ctx->launches += 2;
   }
   return DIRAC_OK;
@@ -192,6 +217,10 @@ static dirac_status observables_impl(dirac_ctx* ctx, dirac_obs* out, double* den
     CK(cudaMemcpyAsync(density_host, ctx->density, n * sizeof(double), cudaMemcpyDeviceToHost, st),
        "copy density");
   CK(cudaStreamSynchronize(st), "synchronize");
+  {
+    dirac_status de = device_error(ctx);
+    if (de != DIRAC_OK) return de;
+  }
   out->norm = r[0];
   out->norm_gamma = r[1];
   out->energy = r[2];
@@ -230,6 +259,8 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
   CK(dalloc(ctx, (void**)&ctx->staging, 2 * n * 2 * sizeof(double)), "allocate staging");
   CK(dalloc(ctx, (void**)&ctx->partials, 4 * sizeof(double) * observables_blocks(n)), "allocate");
   CK(dalloc(ctx, (void**)&ctx->result, 4 * sizeof(double)), "allocate");
+  CK(dalloc(ctx, (void**)&ctx->d_err, sizeof(int)), "allocate");
+  CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st), "clear error flag");
 
   // metric upload: the staging buffer holds the three fields during creation
   double* gdev[3] = {nullptr, nullptr, nullptr};
@@ -422,6 +453,7 @@ dirac_status dirac_get_state(dirac_ctx* ctx, double* psi_out, int on_device) {
                        ctx->stream),
        "download state");
     CK(cudaStreamSynchronize(ctx->stream), "download state");
+    return device_error(ctx);
   }
   return DIRAC_OK;
 }
@@ -447,7 +479,7 @@ dirac_status dirac_observables(dirac_ctx* ctx, dirac_obs* out, double* density_o
 dirac_status dirac_synchronize(dirac_ctx* ctx) {
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
   CK(cudaStreamSynchronize(ctx->stream), "synchronize");
-  return DIRAC_OK;
+  return device_error(ctx);
 }
 
 const char* dirac_last_error(const dirac_ctx* ctx) {
@@ -466,8 +498,8 @@ dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
   const int t[2] = {threads_x_pass, threads_y_pass};
   for (int k = 0; k < 2; ++k)
-    if (t[k] != 0 && t[k] != 256 && t[k] != 512)
-      return fail(ctx, DIRAC_EINVAL, "threads must be 0 (default), 256 or 512");
+    if (t[k] != 0 && t[k] != 256 && t[k] != 512 && t[k] != 1024)
+      return fail(ctx, DIRAC_EINVAL, "threads must be 0 (default), 256, 512 or 1024");
   ctx->threads_x = threads_x_pass;
   ctx->threads_y = threads_y_pass;
   return DIRAC_OK;

@@ -14,7 +14,8 @@ namespace dgb {
 void set_global_error(const std::string& msg);
 
 // Enqueues one fused line pass (MODE_STEP or MODE_DERIV). opt selects the CTA shape:
-// 0 = about 256 threads per CTA, 1 = 512 threads (step mode only).
+// 0 = about 256 threads per CTA, 1 = 512 threads, 2 = the persistent prefetching
+// variant (complex64 step mode, lines of 256..4096 points; otherwise as 1).
 template <typename T>
 cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st);
 // Elements per thread (8 or 16) the line pass uses for line length L; the twiddle table

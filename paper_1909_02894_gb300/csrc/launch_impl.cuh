@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "persist_pass.cuh"
 
 namespace dgb {
 
@@ -87,10 +88,55 @@ static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) 
   }
 }
 
+static int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cached[dev]) cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev);
+  return cached[dev];
+}
+
+// Persistent prefetching variant (complex64 step mode, 256..4096-point lines): one
+// 1024-thread CTA per SM, at most one per group of 4096 points.
+template <int L>
+static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st) {
+  using PG = PGeo<float, L>;
+  if (!a.err || a.n_lines % PG::LPI != 0) return cudaErrorInvalidValue;
+  auto kern = line_pass_persistent<float, L>;
+  static bool configured[64] = {false};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (!configured[dev]) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG::SMEM);
+    if (e != cudaSuccess) return e;
+    configured[dev] = true;
+  }
+  const int groups = a.n_lines / PG::LPI;
+  int grid = sm_count();
+  if (grid <= 0) return cudaErrorInvalidDevice;
+  if (grid > groups) grid = groups;
+  kern<<<grid, PG::THREADS, PG::SMEM, st>>>(a, groups, a.err);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st) {
   if (mode == MODE_DERIV) return dispatch<T, MODE_DERIV>(a, 0, st);
-  return dispatch<T, MODE_STEP>(a, opt, st);
+  if constexpr (sizeof(T) == 4) {
+    if (opt == 2) {
+      switch (a.L) {
+        case 256: return launch_persist<256>(a, st);
+        case 512: return launch_persist<512>(a, st);
+        case 1024: return launch_persist<1024>(a, st);
+        case 2048: return launch_persist<2048>(a, st);
+        case 4096: return launch_persist<4096>(a, st);
+        default: break;
+      }
+    }
+  }
+  return dispatch<T, MODE_STEP>(a, opt >= 1 ? 1 : 0, st);
 }
 
 template <typename T>

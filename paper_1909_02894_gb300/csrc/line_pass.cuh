@@ -47,6 +47,7 @@ struct LinePassArgs {
   const T* beta;        // b - 1 per input point, or nullptr (b = 1)
   const Q4<T>* u_load;  // U applied to psi when it is read, or nullptr
   const Q4<T>* u_store; // U applied to psi_new before the store, or nullptr
+  int* err;             // device error flag (persistent variant: bounded-wait timeouts)
 };
 
 // Read-only cached loads of the table types.
@@ -252,10 +253,27 @@ __device__ __forceinline__ void pass_compute(Cx<T> (&v)[E], int j, const Cx<T>* 
       if constexpr (NS > 1) {
         const int k = (j + u * J) & (NS - 1);
         const Cx<T>* twk = tw + tw_offset(NS, E) + k;
+        if constexpr (sizeof(T) == 4 && (R == 8 || R == 4)) {
+          // FP32 radix-8/4: W^k, W^2k and W^4k from the table, the others as products of
+          // two or three of them (at most two extra roundings per twiddle)
+          Cx<T> w[8];
+          w[1] = ldg_cx(twk);
+          w[2] = ldg_cx(twk + NS);
+          w[3] = cmul(w[1], w[2]);
+          if constexpr (R == 8) {
+            w[4] = ldg_cx(twk + 3 * NS);
+            w[5] = cmul(w[4], w[1]);
+            w[6] = cmul(w[4], w[2]);
+            w[7] = cmul(w[4], w[3]);
+          }
 #pragma unroll
-        for (int t = 1; t < R; ++t) {
-          const Cx<T> w = ldg_cx(twk + (t - 1) * NS);
-          x[t] = INV ? cmulc(x[t], w) : cmul(x[t], w);
+          for (int t = 1; t < R; ++t) x[t] = INV ? cmulc(x[t], w[t]) : cmul(x[t], w[t]);
+        } else {
+#pragma unroll
+          for (int t = 1; t < R; ++t) {
+            const Cx<T> w = ldg_cx(twk + (t - 1) * NS);
+            x[t] = INV ? cmulc(x[t], w) : cmul(x[t], w);
+          }
         }
       }
       dftR<T, R, INV>(x);

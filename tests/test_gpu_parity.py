@@ -196,3 +196,25 @@ def test_norm_conserved_in_flat_space_on_gpu():
         s.step(500, w.dt)
         n1 = s.observables()["norm"]
     assert abs(n1 / n0 - 1.0) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PID)
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("nx,ny", [(512, 256), (1024, 2048), (4096, 256), (256, 4096)])
+def test_every_cta_shape_matches_oracle(prec, threads, nx, ny):
+    """All launch shapes, including the persistent prefetching pass (1024; complex64,
+    lines of 256..4096 points), give the oracle's result."""
+    ax, ay = 0.1 * nx, 0.1 * ny
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g = 1.0 + 0.15 * np.exp(-((X - 0.2 * ax) ** 2 + Y ** 2) / (0.1 * ax * ay))
+    psi0 = W.wave_packet(nx, ny, ax, ay, 0.05 * min(ax, ay) + 1.0, (1.2, 0.4))
+    w = W.Workload("shape", nx, ny, ax, ay, np.ones((ny, nx)), g, 1.0 + 0.5 * (g - 1.0),
+                   mass=0.3, c=1.0, pml_width_x=nx // 32, pml_width_y=ny // 32, pml_type=1,
+                   sigma0=1.0, theta=0.0, psi0=psi0, dt=0.05, steps=4)
+    ref = oracle_run(w, 4)
+    with D.Simulation(w, precision=prec) as s:
+        D.dirac_set_launch(s.ctx, threads, threads)
+        s.set_state(w.psi0)
+        s.step(4, w.dt)
+        got = s.get_state()
+    assert W.rel_l2(got, ref) <= TOL[prec]
