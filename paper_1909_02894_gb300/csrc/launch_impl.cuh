@@ -97,28 +97,44 @@ static int sm_count() {
 }
 
 // Persistent prefetching variant (complex64 step mode, 256..4096-point lines): one
-// 1024-thread CTA per SM, at most one per group of 4096 points.
+// 1024-thread CTA per SM (clusters of 4 / LPI CTAs for 2048- and 4096-point lines), as
+// many as can be resident, at most one per group of 4096 points.
 template <int L>
 static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st) {
   using PG = PGeo<float, L>;
-  if (!a.err || a.n_lines % PG::LPI != 0) return cudaErrorInvalidValue;
+  if (!a.err || a.n_lines % PG::GL != 0) return cudaErrorInvalidValue;
   auto kern = line_pass_persistent<float, L>;
-  static bool configured[64] = {false};
+  static int max_clusters[64] = {0};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  if (!configured[dev]) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(PG::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = PG::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = PG::CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (!max_clusters[dev]) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG::SMEM);
     if (e != cudaSuccess) return e;
-    configured[dev] = true;
+    cfg.gridDim = dim3(PG::CS * 64, 1, 1);
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n <= 0) return cudaErrorInvalidConfiguration;
+    max_clusters[dev] = n;
   }
   const int groups = a.n_lines / PG::LPI;
-  int grid = sm_count();
-  if (grid <= 0) return cudaErrorInvalidDevice;
-  if (grid > groups) grid = groups;
-  kern<<<grid, PG::THREADS, PG::SMEM, st>>>(a, groups, a.err);
-  return cudaGetLastError();
+  int clusters = max_clusters[dev];
+  if (clusters > groups / PG::CS) clusters = groups / PG::CS;
+  cfg.gridDim = dim3(clusters * PG::CS, 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, a, groups, a.err);
 }
 
 template <typename T>

@@ -8,10 +8,14 @@
 // epilogue are those of line_pass_kernel (eigencomponent per thread, radix-8 passes);
 // the spinor values for the load and for the epilogue come from shared memory, so the
 // only global-memory latency left in a group's critical path is the L2 hit of its b - 1
-// and U values. The output leaves in the transposed layout as LPI-line segments.
+// and U values. The output leaves in the transposed layout as segments of LPI lines; for
+// 4096-point lines the CTAs run as clusters of 4 that gather their staged lines through
+// distributed shared memory into 4-line segments.
 //
 // Every wait on an mbarrier is bounded: if one runs out, the CTA records an error code
-// in *err, waits (bounded) for the copy it issued itself and returns.
+// in *err, stops issuing copies and transforming, keeps taking part in the cluster
+// barriers until its peers finish (so none of them waits forever), waits (bounded) for
+// the copy it issued itself and returns.
 #pragma once
 #include "line_pass.cuh"
 
@@ -23,6 +27,11 @@ struct PGeo {
   static constexpr int THREADS = 1024;
   static constexpr int TPL = 2 * L / E;
   static constexpr int LPI = THREADS / TPL;  // lines per group
+  // CTAs per cluster: 4 for 4096-point lines (64-B output segments measured faster than
+  // 16-B ones); shorter lines write LPI-line segments without a cluster (the cluster
+  // barriers cost more than they saved at 2048 points).
+  static constexpr int CS = L == 4096 ? 4 : 1;
+  static constexpr int GL = LPI * CS;               // lines per output segment
   using G = Geo<T, L, LPI, E>;               // FFT buffer plan (padded, conflict-free)
   static constexpr size_t F_BYTES = ((G::SMEM + 127) / 128) * 128;
   static constexpr size_t PSI_BYTES = (size_t)LPI * L * sizeof(Q4<T>);
@@ -40,7 +49,7 @@ __global__ void __launch_bounds__(1024, 1)
     line_pass_persistent(LinePassArgs<T> a, int n_groups, int* __restrict__ err) {
   using PG = PGeo<T, L>;
   using Gm = typename PG::G;
-  constexpr int E = PG::E, J = L / E, LPI = PG::LPI;
+  constexpr int E = PG::E, J = L / E, LPI = PG::LPI, CS = PG::CS, GL = PG::GL;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   Cx<T>* fbuf = reinterpret_cast<Cx<T>*>(smem_raw);
   Q4<T>* psi_buf[2] = {reinterpret_cast<Q4<T>*>(smem_raw + PG::F_BYTES),
@@ -57,9 +66,14 @@ __global__ void __launch_bounds__(1024, 1)
   constexpr uint32_t GROUP_BYTES = (uint32_t)(LPI * L * sizeof(Q4<T>));
   constexpr uint32_t BETA_BYTES = (uint32_t)(LPI * L * sizeof(T));
   constexpr uint32_t U_BYTES = GROUP_BYTES;
+  // cluster geometry: super-group s = lines [s GL, s GL + GL); CTA rank q owns group s CS + q
+  int rank = 0;
+  if constexpr (CS > 1) rank = (int)cg::this_cluster().block_rank();
+  const int cluster_id = blockIdx.x / CS, n_clusters = gridDim.x / CS;
+  const int n_super = n_groups / CS;
 
-  auto issue = [&](int g, int slot) {
-    const size_t first = (size_t)g * LPI * L;
+  auto issue = [&](int grp, int slot) {
+    const size_t first = (size_t)grp * LPI * L;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bars[slot], GROUP_BYTES);
     bulk_copy_g2s(psi_buf[slot], a.in + first, GROUP_BYTES, &bars[slot]);
@@ -74,89 +88,107 @@ __global__ void __launch_bounds__(1024, 1)
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0 && (int)blockIdx.x < n_groups) issue(blockIdx.x, 0);
+  if (tid == 0 && cluster_id < n_super) issue(cluster_id * CS + rank, 0);
 
+  bool failed = false;      // uniform across the CTA
+  int pending = -1;         // slot of a copy issued and not yet waited for (after a failure)
+  uint32_t pending_par = 0; // the phase parity that copy completes
   int it = 0;
-  for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++it) {
+  for (int s = cluster_id; s < n_super; s += n_clusters, ++it) {
     const int b = it & 1;
-    const bool has_next = g + (int)gridDim.x < n_groups;
-    if (tid == 0 && has_next) issue(g + gridDim.x, b ^ 1);
-
-    const bool ok = mbar_wait_bounded(&bars[b], (it >> 1) & 1, kWaitTries);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        atomicExch(err, kErrTimeout);
-        if (has_next) mbar_wait_bounded(&bars[b ^ 1], ((it + 1) >> 1) & 1, kWaitTries);
+    const int g = s * CS + rank;
+    const bool has_next = s + n_clusters < n_super;
+    if (!failed) {
+      if (tid == 0 && has_next) issue((s + n_clusters) * CS + rank, b ^ 1);
+      const bool ok = mbar_wait_bounded(&bars[b], (it >> 1) & 1, kWaitTries);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        if (tid == 0) atomicExch(err, kErrTimeout);
+        pending = has_next ? (b ^ 1) : -1;
+        pending_par = ((it + 1) >> 1) & 1;
       }
-      return;
     }
-
-    const size_t row = ((size_t)g * LPI + lcta) * L;
-    const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_buf[b] + (size_t)lcta * L) + c;
-    Cx<T> v[E];
+    if (!failed) {
+      const size_t row = ((size_t)g * LPI + lcta) * L;
+      const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_buf[b] + (size_t)lcta * L) + c;
+      Cx<T> v[E];
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int i = j + m * J;
-      Cx<T> own = src_c[2 * i];
-      Cx<T> oth = shfl_pair(own);
-      if (a.u_load) {
-        own = apply_u_row(ldg_q4(a.u_load + row + i), own, oth, c);
-        oth = shfl_pair(own);
+      for (int m = 0; m < E; ++m) {
+        const int i = j + m * J;
+        Cx<T> own = src_c[2 * i];
+        Cx<T> oth = shfl_pair(own);
+        if (a.u_load) {
+          own = apply_u_row(ldg_q4(a.u_load + row + i), own, oth, c);
+          oth = shfl_pair(own);
+        }
+        const Cx<T> p1 = c ? oth : own, p2 = c ? own : oth;
+        if (a.sigma == 0) v[m] = {p1.re + sg * p2.re, p1.im + sg * p2.im};
+        else v[m] = {p1.re + sg * p2.im, p1.im - sg * p2.re};
       }
-      const Cx<T> p1 = c ? oth : own, p2 = c ? own : oth;
-      if (a.sigma == 0) v[m] = {p1.re + sg * p2.re, p1.im + sg * p2.im};
-      else v[m] = {p1.re + sg * p2.im, p1.im - sg * p2.re};
-    }
 
-    fft_passes<T, L, E, false>(v, buf, j, a.tw);
+      fft_passes<T, L, E, false>(v, buf, j, a.tw);
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      if ((m & 3) == 0) asm volatile("" ::: "memory");
-      const Q4<T> q = ldg_q4(a.mult + j + m * J);
-      const T vr = v[m].re, vi = v[m].im;
-      const T sh = -sg * q.z, sl = -sg * q.w;
-      v[m] = {q.x * vr + ((q.y * vr - sl * vi) - sh * vi),
-              q.x * vi + ((q.y * vi + sl * vr) + sh * vr)};
-    }
-    fft_passes<T, L, E, true>(v, buf, j, a.tw);
+      for (int m = 0; m < E; ++m) {
+        if ((m & 3) == 0) asm volatile("" ::: "memory");
+        const Q4<T> q = ldg_q4(a.mult + j + m * J);
+        const T vr = v[m].re, vi = v[m].im;
+        const T sh = -sg * q.z, sl = -sg * q.w;
+        v[m] = {q.x * vr + ((q.y * vr - sl * vi) - sh * vi),
+                q.x * vi + ((q.y * vi + sl * vr) + sh * vr)};
+      }
+      fft_passes<T, L, E, true>(v, buf, j, a.tw);
 
-    __syncthreads();  // the FFT buffer becomes the staging buffer
-    Q4<T>* stage = reinterpret_cast<Q4<T>*>(smem_raw);
-    Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
+      __syncthreads();  // the FFT buffer becomes the staging buffer
+      Q4<T>* stage = reinterpret_cast<Q4<T>*>(smem_raw);
+      Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-      if ((m & 3) == 0) asm volatile("" ::: "memory");
-      const int i = j + m * J;
-      const size_t gi = row + i;
-      const Cx<T> oth = shfl_pair(v[m]);
-      const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
-      Cx<T> d;
-      if (c == 0) d = cadd(dp, dm);
-      else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
-      Cx<T> p = src_c[2 * i];
-      if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
-      const T bm1 = a.beta ? a.beta[gi] : T(0);
-      Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
-      if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
-      my_stage[2 * i] = o;
+      for (int m = 0; m < E; ++m) {
+        if ((m & 3) == 0) asm volatile("" ::: "memory");
+        const int i = j + m * J;
+        const size_t gi = row + i;
+        const Cx<T> oth = shfl_pair(v[m]);
+        const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
+        Cx<T> d;
+        if (c == 0) d = cadd(dp, dm);
+        else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+        Cx<T> p = src_c[2 * i];
+        if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
+        const T bm1 = a.beta ? a.beta[gi] : T(0);
+        Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+        if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
+        my_stage[2 * i] = o;
+      }
     }
-    __syncthreads();
-    // transposed store: out[i][g LPI .. g LPI + LPI)
-    const int line0 = g * LPI;
-    constexpr int NIT = LPI * L / PG::THREADS;
-    Q4<T> val[NIT];
+    // ---- transposed store of the super-group: out[i][s GL .. s GL + GL); CTA rank q
+    // writes rows i of its L/CS slice, reading the owners' staging buffers
+    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    if (!failed) {
+      const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(smem_raw);
+      const int line0 = s * GL;
+      const int i0 = rank * (L / CS);
+      constexpr int NIT = (L / CS) * GL / PG::THREADS;
+      Q4<T> val[NIT];
 #pragma unroll
-    for (int q = 0; q < NIT; ++q) {
-      const int itm = tid + q * PG::THREADS;
-      val[q] = stage[(size_t)(itm % LPI) * (L + 1) + itm / LPI];
-    }
+      for (int q = 0; q < NIT; ++q) {
+        const int itm = tid + q * PG::THREADS;
+        const int gg = itm % GL, owner = gg / LPI;
+        const Q4<T>* src = stage;
+        if constexpr (CS > 1) {
+          if (owner != rank) src = cg::this_cluster().map_shared_rank(stage, owner);
+        }
+        val[q] = src[(size_t)(gg - owner * LPI) * (L + 1) + i0 + itm / GL];
+      }
 #pragma unroll
-    for (int q = 0; q < NIT; ++q) {
-      const int itm = tid + q * PG::THREADS;
-      a.out[(size_t)(itm / LPI) * a.n_lines + line0 + itm % LPI] = val[q];
+      for (int q = 0; q < NIT; ++q) {
+        const int itm = tid + q * PG::THREADS;
+        a.out[(size_t)(i0 + itm / GL) * a.n_lines + line0 + itm % GL] = val[q];
+      }
     }
-    __syncthreads();  // staging and psi_buf[b] are free for the next group
+    // staging and psi_buf[b] are free for the next super-group once every CTA of the
+    // cluster has finished reading
+    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
   }
+  if (failed && tid == 0 && pending >= 0) mbar_wait_bounded(&bars[pending], pending_par, kWaitTries);
 }
 
 }  // namespace dgb
