@@ -204,6 +204,93 @@ def cpu_baseline(w):
             "sample": f"difference of 2-step and 1-step FP64 oracle runs on {w.name}"}
 
 
+def run_batch(args):
+    """Batched uneven mix: 256 instances (128^2..1024^2, weights 0.4/0.3/0.2/0.1), each
+    stepped `--steps` times (default 2000) in one batch of graph-captured ticks, complex64;
+    beside it the plain complex128 single-instance path, each instance alone."""
+    import torch
+
+    import paper_1909_02894_gb300 as D
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    count = args.batch_count
+    ws = W.batch_mix(count=count, steps=args.steps)
+    stream = torch.cuda.Stream()
+    sims = [D.Simulation(w, precision=D.DIRAC_C64, stream=stream.cuda_stream) for w in ws]
+    budget = sum(D.dirac_footprint_bytes(w.nx, w.ny) for w in ws) + (1 << 20)
+    batch = D.dirac_batch_create(budget, D.DIRAC_C64, steps_per_tick=args.tick,
+                                 stream=stream.cuda_stream)
+    pts = sum(w.points for w in ws)
+
+    def run(n_steps):
+        slots = []
+        for s, w in zip(sims, ws):
+            s.set_state(w.psi0)
+            slots.append(D.dirac_batch_submit(batch, s.ctx, n_steps, w.dt))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        while D.dirac_batch_active(batch):
+            D.dirac_batch_run(batch, 1)
+        e1.record(stream)
+        D.dirac_batch_synchronize(batch)
+        torch.cuda.synchronize()
+        for sl in slots:
+            D.dirac_batch_release(batch, sl)
+        return e0.elapsed_time(e1)
+
+    run(max(3, args.warmup))
+    l0 = D.dirac_batch_launch_count(batch)
+    with Clocks(local) as clk:
+        ms = run(args.steps)
+    value = pts * args.steps / (ms * 1e-3)
+    # plain complex128 path, each instance alone, on a bounded sample (one of each size)
+    sample, seen = [], set()
+    for w in ws:
+        if w.nx not in seen:
+            seen.add(w.nx)
+            sample.append(w)
+    plain_steps = 50
+    t_plain = 0.0
+    for w in sample:
+        with D.Simulation(w, precision=D.DIRAC_C128, stream=stream.cuda_stream) as s:
+            s.set_state(w.psi0)
+            s.step(3, w.dt)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(plain_steps, w.dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_plain += e0.elapsed_time(e1) * 1e-3 / plain_steps * sum(
+                x.points for x in ws if x.nx == w.nx) / w.points
+    plain = pts / t_plain
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch-mix-{count}", "precision": "c64 batched",
+                   "sizes": {str(n): sum(1 for w in ws if w.nx == n) for n in W.BATCH_SIZES},
+                   "points_per_step": pts, "steps_per_tick": args.tick,
+                   "l2": "working set larger than L2 (no flush)"},
+        "plain_c128_single_instance": {"value": plain, "unit": UNIT,
+                                       "sample": f"one instance of each size, {plain_steps} steps, "
+                                                 "scaled by the mix's point counts"},
+        "batched_over_plain_c128": value / plain,
+        "clocks": clk.summary(),
+        "gpu_launches": int(D.dirac_batch_launch_count(batch) - l0),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    D.dirac_batch_destroy(batch)
+    for s in sims:
+        s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,9 +300,13 @@ def main():
     ap.add_argument("--workload", default="large-4096")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-solves", type=int, default=3)
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--tick", type=int, default=32)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
+    if args.workload == "batch-mix":
+        return run_batch(args)
 
     import torch
 

@@ -149,6 +149,55 @@ dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_
 /* Number of kernel launches this context has enqueued so far (for accounting). */
 long dirac_launch_count(const dirac_ctx *ctx);
 
+/* Device bytes a context of this size and precision can hold (state, coefficients,
+ * half-step matrices, host-transfer staging, observables scratch). 0 for bad input. */
+size_t dirac_footprint_bytes(const dirac_grid *grid, dirac_precision precision);
+
+/* ---- Batched stepping of many independent contexts (any mix of grid sizes).
+ * Contexts of the same grid size form a class; one tick advances every active context
+ * by up to steps_per_tick steps, each step being, per class, one x-pass and one y-pass
+ * launch over all of that class's active contexts, with the classes on parallel branches
+ * of a CUDA graph captured once per class layout and replayed. Each context computes
+ * exactly what dirac_step(ctx, n_steps, dt) computes (Sec. 5.2 Scheme II); a submitted
+ * context belongs to the batch until it is released and must not be stepped, read or
+ * destroyed meanwhile. Contexts must have the batch's precision. */
+
+/* Creates a batch with a device-memory budget (bytes of dirac_footprint_bytes summed
+ * over the submitted contexts), on cuda_stream (NULL = a stream of its own). */
+dirac_status dirac_batch_create(size_t hbm_budget_bytes, dirac_precision precision,
+                                void *cuda_stream, int steps_per_tick, dirac_batch **out);
+
+/* Admits a context (its state must be set) for n_steps steps of size dt; *slot receives
+ * its handle. DIRAC_ENOMEM when the budget would be exceeded (retry after a release). */
+dirac_status dirac_batch_submit(dirac_batch *batch, dirac_ctx *inst, long n_steps, double dt,
+                                int *slot);
+
+/* Enqueues n_ticks ticks (host returns after enqueueing; the tables of one tick are
+ * prepared while the previous one runs). */
+dirac_status dirac_batch_run(dirac_batch *batch, int n_ticks);
+
+/* *done = 1 once every step of the slot's context has finished on the device.
+ * DIRAC_ETIMEOUT if a bounded device wait ran out. */
+dirac_status dirac_batch_poll(dirac_batch *batch, int slot, int *done);
+
+/* Returns the slot (and its budget); a context still running is cancelled after the
+ * steps already enqueued. The context is the caller's again. */
+dirac_status dirac_batch_release(dirac_batch *batch, int slot);
+
+/* Waits for all enqueued ticks; DIRAC_ETIMEOUT as for dirac_synchronize. */
+dirac_status dirac_batch_synchronize(dirac_batch *batch);
+
+/* Number of contexts still stepping. */
+int dirac_batch_active(const dirac_batch *batch);
+
+/* Kernels the batch has enqueued (each kernel node of a replayed tick graph counts). */
+long dirac_batch_launch_count(const dirac_batch *batch);
+
+const char *dirac_batch_last_error(const dirac_batch *batch);
+
+/* Waits for enqueued work and frees the batch (not the contexts). NULL is allowed. */
+void dirac_batch_destroy(dirac_batch *batch);
+
 /* Norms of a device spinor without allocating device memory. The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc where they need a norm --
  * code running during CUDA stream capture (allocation is not allowed there), services

@@ -27,7 +27,10 @@ DIRAC_CONN_COVARIANT, DIRAC_CONN_PAPER_2D, DIRAC_CONN_NONE = 0, 1, 2
 ABI_SYMBOLS = (
     "dirac_create", "dirac_set_state", "dirac_get_state", "dirac_step",
     "dirac_observables", "dirac_synchronize", "dirac_last_error", "dirac_destroy",
-    "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc",
+    "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc", "dirac_footprint_bytes",
+    "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
+    "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
+    "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
 )
 
 
@@ -95,6 +98,25 @@ def lib():
         L.dirac_launch_count.restype = l
         L.dirac_norms_noalloc.argtypes = [vp, vp, i, i, d, d, vp, vp]
         L.dirac_norms_noalloc.restype = C.c_int
+        L.dirac_footprint_bytes.argtypes = [C.POINTER(_Grid), i]
+        L.dirac_footprint_bytes.restype = C.c_size_t
+        L.dirac_batch_create.argtypes = [C.c_size_t, i, vp, i, C.POINTER(vp)]
+        L.dirac_batch_submit.argtypes = [vp, vp, l, d, C.POINTER(i)]
+        L.dirac_batch_run.argtypes = [vp, i]
+        L.dirac_batch_poll.argtypes = [vp, i, C.POINTER(i)]
+        L.dirac_batch_release.argtypes = [vp, i]
+        L.dirac_batch_synchronize.argtypes = [vp]
+        for f in ("dirac_batch_create", "dirac_batch_submit", "dirac_batch_run",
+                  "dirac_batch_poll", "dirac_batch_release", "dirac_batch_synchronize"):
+            getattr(L, f).restype = C.c_int
+        L.dirac_batch_active.argtypes = [vp]
+        L.dirac_batch_active.restype = C.c_int
+        L.dirac_batch_launch_count.argtypes = [vp]
+        L.dirac_batch_launch_count.restype = l
+        L.dirac_batch_last_error.argtypes = [vp]
+        L.dirac_batch_last_error.restype = C.c_char_p
+        L.dirac_batch_destroy.argtypes = [vp]
+        L.dirac_batch_destroy.restype = None
         for f in ("dirac_create", "dirac_set_state", "dirac_get_state", "dirac_step",
                   "dirac_observables", "dirac_synchronize", "dirac_set_launch"):
             getattr(L, f).restype = C.c_int
@@ -206,6 +228,67 @@ def dirac_norms_noalloc(psi, weight, ax: float, ay: float, out, stream=None):
         wp = weight.data_ptr()
     _check(lib().dirac_norms_noalloc(psi.data_ptr(), wp, nx, ny, float(ax), float(ay),
                                      out.data_ptr(), stream), None)
+
+
+def dirac_footprint_bytes(nx: int, ny: int, precision: int = DIRAC_C64) -> int:
+    return int(lib().dirac_footprint_bytes(C.byref(_Grid(nx, ny)), precision))
+
+
+def dirac_batch_last_error(batch) -> str:
+    s = lib().dirac_batch_last_error(batch)
+    return s.decode() if s else ""
+
+
+def _bcheck(status, batch):
+    if status != DIRAC_OK:
+        raise DiracError(status, dirac_batch_last_error(batch))
+
+
+def dirac_batch_create(budget_bytes: int, precision: int = DIRAC_C64, steps_per_tick: int = 32,
+                       stream: Optional[int] = None):
+    out = C.c_void_p()
+    st = lib().dirac_batch_create(int(budget_bytes), precision, stream, int(steps_per_tick),
+                                  C.byref(out))
+    if st != DIRAC_OK:
+        raise DiracError(st, "dirac_batch_create failed")
+    return out.value
+
+
+def dirac_batch_submit(batch, ctx, n_steps: int, dt: float) -> int:
+    slot = C.c_int(-1)
+    _bcheck(lib().dirac_batch_submit(batch, ctx, int(n_steps), float(dt), C.byref(slot)), batch)
+    return slot.value
+
+
+def dirac_batch_run(batch, n_ticks: int = 1):
+    _bcheck(lib().dirac_batch_run(batch, int(n_ticks)), batch)
+
+
+def dirac_batch_poll(batch, slot: int) -> bool:
+    done = C.c_int(0)
+    _bcheck(lib().dirac_batch_poll(batch, int(slot), C.byref(done)), batch)
+    return bool(done.value)
+
+
+def dirac_batch_release(batch, slot: int):
+    _bcheck(lib().dirac_batch_release(batch, int(slot)), batch)
+
+
+def dirac_batch_synchronize(batch):
+    _bcheck(lib().dirac_batch_synchronize(batch), batch)
+
+
+def dirac_batch_active(batch) -> int:
+    return int(lib().dirac_batch_active(batch))
+
+
+def dirac_batch_launch_count(batch) -> int:
+    return int(lib().dirac_batch_launch_count(batch))
+
+
+def dirac_batch_destroy(batch):
+    if batch:
+        lib().dirac_batch_destroy(batch)
 
 
 def dirac_destroy(ctx):

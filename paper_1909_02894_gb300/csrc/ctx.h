@@ -1,0 +1,48 @@
+// Definition of the opaque context (library-internal; shared by the ABI and the batch).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dirac.h"
+
+struct dirac_ctx {
+  int nx = 0, ny = 0;
+  double ax = 0, ay = 0, mass = 0, c = 1;
+  dirac_precision prec = DIRAC_C64;
+  int conn = 0;
+  dirac_absorber abs = {0, 0, 1, 1.0, 0.0};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  bool u_identity = false;  // no mass and no connection: U = I exactly
+
+  // FP64 fields in the normal layout [ny][nx]
+  double *a1 = nullptr, *a2 = nullptr, *meff = nullptr, *w = nullptr, *omx = nullptr,
+         *omy = nullptr;
+  double *sxinv = nullptr, *syinv = nullptr;
+  // state and per-pass coefficients in the state precision
+  void *psi = nullptr, *psiT = nullptr;
+  void *beta1 = nullptr, *beta2T = nullptr;
+  void *u_n = nullptr, *u_t = nullptr, *u2_t = nullptr;
+  void *tw_x = nullptr, *tw_y = nullptr, *mult_x = nullptr, *mult_y = nullptr,
+       *dmult_x = nullptr, *dmult_y = nullptr;
+  double* staging = nullptr;  // [2][ny][nx] complex128 for host transfers
+  void *scratch1 = nullptr, *scratch2 = nullptr;
+  double *partials = nullptr, *result = nullptr, *density = nullptr;
+
+  int* d_err = nullptr;       // device error flag written by bounded waits
+  double dt_cached = 0.0;
+  bool state_set = false;
+  int threads_x = 0, threads_y = 0;
+  long launches = 0;
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+// Library-internal helpers implemented in dirac_api.cu.
+dirac_status dgb_tables_for_dt(dirac_ctx* ctx, double dt);
+size_t dgb_footprint_bytes(int nx, int ny, dirac_precision prec);
+// Launch option (0, 1, 2 = persistent) for a pass of line length L.
+int dgb_pass_opt(const dirac_ctx* ctx, int threads, int L);

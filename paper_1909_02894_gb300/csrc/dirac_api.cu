@@ -11,43 +11,12 @@
 #include <vector>
 
 #include "../../include/dirac.h"
+#include "ctx.h"
 #include "internal.h"
 
 using namespace dgb;
 
-struct dirac_ctx {
-  int nx = 0, ny = 0;
-  double ax = 0, ay = 0, mass = 0, c = 1;
-  dirac_precision prec = DIRAC_C64;
-  int conn = 0;
-  dirac_absorber abs = {0, 0, 1, 1.0, 0.0};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  int device = 0;
-  bool u_identity = false;  // no mass and no connection: U = I exactly
 
-  // FP64 fields in the normal layout [ny][nx]
-  double *a1 = nullptr, *a2 = nullptr, *meff = nullptr, *w = nullptr, *omx = nullptr,
-         *omy = nullptr;
-  double *sxinv = nullptr, *syinv = nullptr;
-  // state and per-pass coefficients in the state precision
-  void *psi = nullptr, *psiT = nullptr;
-  void *beta1 = nullptr, *beta2T = nullptr;
-  void *u_n = nullptr, *u_t = nullptr, *u2_t = nullptr;
-  void *tw_x = nullptr, *tw_y = nullptr, *mult_x = nullptr, *mult_y = nullptr,
-       *dmult_x = nullptr, *dmult_y = nullptr;
-  double* staging = nullptr;  // [2][ny][nx] complex128 for host transfers
-  void *scratch1 = nullptr, *scratch2 = nullptr;
-  double *partials = nullptr, *result = nullptr, *density = nullptr;
-
-  int* d_err = nullptr;       // device error flag written by bounded waits
-  double dt_cached = 0.0;
-  bool state_set = false;
-  int threads_x = 0, threads_y = 0;
-  long launches = 0;
-  std::string err;
-  std::vector<void*> allocs;
-};
 
 static thread_local std::string g_create_error;
 
@@ -332,6 +301,29 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
   return DIRAC_OK;
 }
 
+// ------------------------------------------------------------------ library-internal
+dirac_status dgb_tables_for_dt(dirac_ctx* ctx, double dt) {
+  return ctx->prec == DIRAC_C64 ? tables_for_dt<float>(ctx, dt) : tables_for_dt<double>(ctx, dt);
+}
+
+int dgb_pass_opt(const dirac_ctx* ctx, int threads, int L) { return pass_opt(ctx, threads, L); }
+
+// Device bytes a context of this size holds at most (creation, state, half-step
+// matrices, staging for host transfers, observables scratch and density).
+size_t dgb_footprint_bytes(int nx, int ny, dirac_precision prec) {
+  const size_t n = (size_t)nx * ny;
+  const size_t r = prec == DIRAC_C64 ? 4 : 8, q4 = 4 * r;
+  size_t per_point = 6 * sizeof(double)   // a1, a2, meff, w, omx, omy
+                     + 2 * q4             // psi, psiT
+                     + 2 * r              // b - 1 (both layouts)
+                     + 3 * q4             // U (two layouts), U^2
+                     + 4 * sizeof(double) // staging (complex128 spinor)
+                     + 2 * q4             // observables scratch
+                     + sizeof(double);    // density
+  size_t per_line = (size_t)(nx + ny) * (sizeof(double) + 3 * q4);
+  return n * per_point + per_line + 4 * sizeof(double) * 2048 + 4096;
+}
+
 // ------------------------------------------------------------------------ the ABI
 extern "C" {
 
@@ -506,5 +498,10 @@ dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_
 }
 
 long dirac_launch_count(const dirac_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+size_t dirac_footprint_bytes(const dirac_grid* grid, dirac_precision precision) {
+  if (!grid || grid->nx <= 0 || grid->ny <= 0) return 0;
+  return dgb_footprint_bytes(grid->nx, grid->ny, precision);
+}
 
 }  // extern "C"

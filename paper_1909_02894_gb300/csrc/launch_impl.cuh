@@ -34,7 +34,7 @@ static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
     configured[dev] = true;
   }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(a.n_lines / LPC, 1, 1);
+  cfg.gridDim = dim3((a.inst ? a.inst_capacity : 1) * (a.n_lines / LPC), 1, 1);
   cfg.blockDim = dim3(Gm::THREADS, 1, 1);
   cfg.dynamicSmemBytes = Gm::SMEM;
   cfg.stream = st;
@@ -130,7 +130,7 @@ static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st)
     if (n <= 0) return cudaErrorInvalidConfiguration;
     max_clusters[dev] = n;
   }
-  const int groups = a.n_lines / PG::LPI;
+  const int groups = (a.inst ? a.inst_capacity : 1) * (a.n_lines / PG::LPI);
   int clusters = max_clusters[dev];
   if (clusters > groups / PG::CS) clusters = groups / PG::CS;
   cfg.gridDim = dim3(clusters * PG::CS, 1, 1);

@@ -34,6 +34,18 @@ namespace cg = cooperative_groups;
 
 enum { MODE_STEP = 0, MODE_DERIV = 1 };
 
+// Per-instance pointers of a batched launch (several simulations of the same grid size
+// in one launch); the twiddle table is shared (it depends only on the line length).
+template <typename T>
+struct InstPtrs {
+  const Q4<T>* in;
+  Q4<T>* out;
+  const T* beta;
+  const Q4<T>* u_load;
+  const Q4<T>* u_store;
+  const Q4<T>* mult;
+};
+
 template <typename T>
 struct LinePassArgs {
   const Q4<T>* in;      // [n_lines][L] spinor points
@@ -48,7 +60,23 @@ struct LinePassArgs {
   const Q4<T>* u_load;  // U applied to psi when it is read, or nullptr
   const Q4<T>* u_store; // U applied to psi_new before the store, or nullptr
   int* err;             // device error flag (persistent variant: bounded-wait timeouts)
+  const InstPtrs<T>* inst;  // batched launch: per-instance pointers (overrides the above)
+  const int* n_inst;        // batched launch: number of active instances (device memory)
+  int inst_capacity;        // batched launch: table entries (host side, sizes the grid)
 };
+
+// Batched launches: a block (or group) of lines belongs to instance `k`; take that
+// instance's pointers.
+template <typename T>
+__device__ __forceinline__ void bind_instance(LinePassArgs<T>& a, int k) {
+  const InstPtrs<T> p = a.inst[k];
+  a.in = p.in;
+  a.out = p.out;
+  a.beta = p.beta;
+  a.u_load = p.u_load;
+  a.u_store = p.u_store;
+  a.mult = p.mult;
+}
 
 // Read-only cached loads of the table types.
 __device__ __forceinline__ Cx<float> ldg_cx(const Cx<float>* p) {
@@ -367,12 +395,22 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cx<T>* smem = reinterpret_cast<Cx<T>*>(smem_raw);
 
+  // batched launch: blocks of one instance are consecutive (whole clusters), and blocks
+  // past the active instances leave at once (together with their cluster)
+  int blk = blockIdx.x;
+  if (a.inst) {
+    const int per_inst = a.n_lines / LPC;
+    const int k = blk / per_inst;
+    if (k >= *a.n_inst) return;
+    bind_instance(a, k);
+    blk -= k * per_inst;
+  }
   const int tid = threadIdx.x;
   const int lcta = tid / Gm::TPL;
   const int r = tid - lcta * Gm::TPL;
   const int c = r & 1;        // eigencomponent (step) or component (derivative)
   const int j = r >> 1;
-  const size_t row = (size_t)(blockIdx.x * LPC + lcta) * L;
+  const size_t row = (size_t)(blk * LPC + lcta) * L;
   Cx<T>* buf = smem + lcta * Gm::STRIDE + c * Gm::COMP;
   const T sg = c ? T(-1) : T(1);
   // component c of point gi (the pair of threads reads one 2x8-B / 2x16-B point together)
@@ -468,7 +506,7 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
   } else {
     __syncthreads();
   }
-  const int line0 = (blockIdx.x / CS) * GL;
+  const int line0 = (blk / CS) * GL;
   const int i0 = rank * ROWS;
   constexpr int HALF = Gm::NIT / 2;
 #pragma unroll

@@ -70,16 +70,32 @@ __global__ void __launch_bounds__(1024, 1)
   int rank = 0;
   if constexpr (CS > 1) rank = (int)cg::this_cluster().block_rank();
   const int cluster_id = blockIdx.x / CS, n_clusters = gridDim.x / CS;
-  const int n_super = n_groups / CS;
 
+  // batched launch: groups of instance k are [k gpi, (k + 1) gpi)
+  const int gpi = a.n_lines / LPI;
+  if (a.inst) n_groups = *a.n_inst * gpi;
+  const int n_super = n_groups / CS;
+  const LinePassArgs<T> a0 = a;
+  auto args_of = [&](int grp, size_t* first) {
+    LinePassArgs<T> x = a0;
+    int lg = grp;
+    if (a0.inst) {
+      const int k = grp / gpi;
+      bind_instance(x, k);
+      lg = grp - k * gpi;
+    }
+    *first = (size_t)lg * LPI * L;
+    return x;
+  };
   auto issue = [&](int grp, int slot) {
-    const size_t first = (size_t)grp * LPI * L;
+    size_t first;
+    const LinePassArgs<T> x = args_of(grp, &first);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bars[slot], GROUP_BYTES);
-    bulk_copy_g2s(psi_buf[slot], a.in + first, GROUP_BYTES, &bars[slot]);
-    if (a.beta) bulk_prefetch_l2(a.beta + first, BETA_BYTES);
-    if (a.u_store) bulk_prefetch_l2(a.u_store + first, U_BYTES);
-    if (a.u_load) bulk_prefetch_l2(a.u_load + first, U_BYTES);
+    bulk_copy_g2s(psi_buf[slot], x.in + first, GROUP_BYTES, &bars[slot]);
+    if (x.beta) bulk_prefetch_l2(x.beta + first, BETA_BYTES);
+    if (x.u_store) bulk_prefetch_l2(x.u_store + first, U_BYTES);
+    if (x.u_load) bulk_prefetch_l2(x.u_load + first, U_BYTES);
   };
 
   if (tid == 0) {
@@ -108,8 +124,10 @@ __global__ void __launch_bounds__(1024, 1)
         pending_par = ((it + 1) >> 1) & 1;
       }
     }
+    size_t gfirst;
+    a = args_of(g, &gfirst);
     if (!failed) {
-      const size_t row = ((size_t)g * LPI + lcta) * L;
+      const size_t row = gfirst + (size_t)lcta * L;
       const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_buf[b] + (size_t)lcta * L) + c;
       Cx<T> v[E];
 #pragma unroll
@@ -164,7 +182,7 @@ __global__ void __launch_bounds__(1024, 1)
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     if (!failed) {
       const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(smem_raw);
-      const int line0 = s * GL;
+      const int line0 = (int)(gfirst / L) - rank * LPI;
       const int i0 = rank * (L / CS);
       constexpr int NIT = (L / CS) * GL / PG::THREADS;
       Q4<T> val[NIT];
