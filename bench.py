@@ -291,6 +291,56 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Strained-graphene request stream through the continuous-batching loop: Poisson
+    arrivals at the configured rate (200/s) over a window of --serve-seconds, grids
+    {256,512,1024,2048}^2, steps U{500..5000}, complex64, 1% FP64-checked; and the same
+    stream at a sustainable rate. Reports p50/p99 latency and throughput."""
+    import torch
+
+    import paper_1909_02894_gb300 as D
+    from paper_1909_02894_gb300 import serve as S
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    out = {}
+    for label, rate, window in (("configured", 200.0, args.serve_seconds),
+                                ("sustainable", args.sustainable_rate, args.sustainable_seconds)):
+        reqs = S.graphene_requests(rate=rate, duration=window, seed=1914)
+        work = sum(r.nx * r.ny * r.steps for r in reqs)
+        srv = S.Server(budget, steps_per_tick=args.tick, stream=stream.cuda_stream)
+        for r in reqs:
+            srv.submit(r)
+        t0 = time.perf_counter()
+        results = srv.run(t0=t0)
+        elapsed = time.perf_counter() - t0
+        srv.close()
+        summ = S.latency_summary(results)
+        summ.update({"rate_per_s": rate, "window_s": window, "throughput": work / elapsed,
+                     "elapsed_s": elapsed, "max_active": srv.max_active,
+                     "admitted_while_busy": srv.admitted_while_busy, "ticks": srv.ticks})
+        checks = S.fp64_check(results, stream=stream.cuda_stream)
+        summ["fp64_check"] = {"requests": len(checks),
+                              "max_rel_l2": max((c["rel_l2"] for c in checks), default=None)}
+        out[label] = summ
+    line = {
+        "metric": "p50/p99 solve ms and grid-point*steps/s (serving)",
+        "value": out["configured"]["throughput"], "unit": UNIT, "n_gpus": world,
+        "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve-graphene", "arrivals": "Poisson",
+                   "sizes": list(W.SERVE_SIZES), "steps": [500, 5000],
+                   "budget_bytes": budget, "steps_per_tick": args.tick},
+        "serving": out,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -302,11 +352,16 @@ def main():
     ap.add_argument("--e2e-solves", type=int, default=3)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--tick", type=int, default=32)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--sustainable-rate", type=float, default=4.0)
+    ap.add_argument("--sustainable-seconds", type=float, default=20.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
     if args.workload == "batch-mix":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
 

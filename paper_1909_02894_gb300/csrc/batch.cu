@@ -40,8 +40,8 @@ struct Class {
   int* h_count = nullptr;
   int* d_count = nullptr;
   cudaStream_t stream = nullptr;
-  const void* tw_x = nullptr;
-  const void* tw_y = nullptr;
+  void* tw_x = nullptr;  // twiddle tables owned by the class (contexts come and go)
+  void* tw_y = nullptr;
 };
 
 struct Slot {
@@ -105,6 +105,8 @@ static void free_class(Class& c) {
   if (c.h_count) cudaFreeHost(c.h_count);
   if (c.d_count) cudaFree(c.d_count);
   if (c.stream) cudaStreamDestroy(c.stream);
+  if (c.tw_x) cudaFree(c.tw_x);
+  if (c.tw_y) cudaFree(c.tw_y);
   c = Class();
 }
 
@@ -369,9 +371,18 @@ dirac_status dirac_batch_submit(dirac_batch* b, dirac_ctx* inst, long n_steps, d
   if (!c.stream) {
     c.nx = inst->nx;
     c.ny = inst->ny;
-    c.tw_x = inst->tw_x;
-    c.tw_y = inst->tw_y;
     BCK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "class stream");
+    const size_t cx = b->prec == DIRAC_C64 ? sizeof(Cx<float>) : sizeof(Cx<double>);
+    BCK(cudaMalloc(&c.tw_x, c.nx * cx), "class twiddles");
+    BCK(cudaMalloc(&c.tw_y, c.ny * cx), "class twiddles");
+    if (b->prec == DIRAC_C64) {
+      BCK(launch_twiddles<float>(c.nx, line_pass_radix<float>(c.nx), (Cx<float>*)c.tw_x, b->stream), "twiddles");
+      BCK(launch_twiddles<float>(c.ny, line_pass_radix<float>(c.ny), (Cx<float>*)c.tw_y, b->stream), "twiddles");
+    } else {
+      BCK(launch_twiddles<double>(c.nx, line_pass_radix<double>(c.nx), (Cx<double>*)c.tw_x, b->stream), "twiddles");
+      BCK(launch_twiddles<double>(c.ny, line_pass_radix<double>(c.ny), (Cx<double>*)c.tw_y, b->stream), "twiddles");
+    }
+    BCK(cudaStreamSynchronize(b->stream), "class twiddles");
   }
   c.members.push_back(s);
   *slot = s;

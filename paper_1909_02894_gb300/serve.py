@@ -1,0 +1,166 @@
+"""Continuous-batching request loop over the batch ABI (dirac_batch_*).
+
+Each request is one simulation (grid, metric, packet, step count). Requests that have
+arrived are admitted as soon as their device footprint fits the budget -- also while
+others are running -- and join the next tick of the shared batch; finished requests are
+retired at once and their memory is freed for the next admissions. Latency is measured
+from arrival to the moment the request's last step has completed on the device.
+
+A seeded subset of requests is checked after the run against the same simulation in
+complex128 (the FP64 path), reported as rel-L2.
+"""
+from __future__ import annotations
+
+import heapq
+import time
+from dataclasses import dataclass, field
+from typing import Callable, List, Optional
+
+import numpy as np
+
+from . import (DIRAC_C64, DIRAC_C128, Simulation, dirac_batch_active, dirac_batch_create,
+               dirac_batch_destroy, dirac_batch_poll, dirac_batch_release, dirac_batch_run,
+               dirac_batch_submit, dirac_batch_synchronize, dirac_footprint_bytes)
+from . import workloads as W
+
+
+@dataclass(order=True)
+class Request:
+    arrival: float
+    rid: int = field(compare=False)
+    make: Callable[[], "W.Workload"] = field(compare=False)
+    nx: int = field(compare=False)
+    ny: int = field(compare=False)
+    steps: int = field(compare=False)
+    check: bool = field(compare=False, default=False)
+
+
+@dataclass
+class Result:
+    rid: int
+    nx: int
+    steps: int
+    arrival: float
+    admitted: float
+    finished: float
+    state: Optional[np.ndarray] = None
+    workload: Optional["W.Workload"] = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+class Server:
+    """One device-memory budget, one batch, requests admitted between ticks."""
+
+    def __init__(self, budget_bytes: int, precision: int = DIRAC_C64, steps_per_tick: int = 32,
+                 stream=None, keep_states: bool = False):
+        self.precision = precision
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.batch = dirac_batch_create(self.budget, precision, steps_per_tick, stream)
+        self.stream = stream
+        self.keep_states = keep_states
+        self.pending: List[Request] = []
+        self.active = {}  # slot -> (request, sim, admitted time)
+        self.results: List[Result] = []
+        self.ticks = 0
+        self.max_active = 0
+        self.admitted_while_busy = 0  # admissions into a batch that already had work
+
+    def close(self):
+        for _, entry in list(self.active.items()):
+            entry[1].close()
+        self.active.clear()
+        dirac_batch_destroy(self.batch)
+        self.batch = None
+
+    def submit(self, req: Request):
+        heapq.heappush(self.pending, req)
+
+    def _admit(self, now: float):
+        while self.pending and self.pending[0].arrival <= now:
+            req = self.pending[0]
+            need = dirac_footprint_bytes(req.nx, req.ny, self.precision)
+            if self.used + need > self.budget:
+                break  # wait for memory; keep arrival order
+            heapq.heappop(self.pending)
+            w = req.make()
+            sim = Simulation(w, precision=self.precision, stream=self.stream)
+            sim.set_state(w.psi0)
+            if self.active:
+                self.admitted_while_busy += 1
+            slot = dirac_batch_submit(self.batch, sim.ctx, req.steps, w.dt)
+            self.used += need
+            self.active[slot] = (req, sim, time.perf_counter(), w)
+
+    def _retire(self):
+        for slot in list(self.active):
+            if dirac_batch_poll(self.batch, slot):
+                req, sim, admitted, w = self.active.pop(slot)
+                done = time.perf_counter()
+                dirac_batch_release(self.batch, slot)
+                state = sim.get_state() if (self.keep_states or req.check) else None
+                sim.close()
+                self.used -= dirac_footprint_bytes(req.nx, req.ny, self.precision)
+                self.results.append(Result(req.rid, req.nx, req.steps, req.arrival, admitted,
+                                           done, state, w if req.check else None))
+
+    def run(self, t0: Optional[float] = None, deadline: Optional[float] = None):
+        """Serve until every submitted request has finished (arrival times are seconds
+        after t0, default now)."""
+        if t0 is None:
+            t0 = time.perf_counter()
+        for r in self.pending:
+            r.arrival += t0
+        heapq.heapify(self.pending)
+        while self.pending or self.active:
+            now = time.perf_counter()
+            if deadline is not None and now - t0 > deadline:
+                raise TimeoutError("serving deadline exceeded")
+            self._admit(now)
+            self.max_active = max(self.max_active, len(self.active))
+            if self.active:
+                dirac_batch_run(self.batch, 1)
+                self.ticks += 1
+                self._retire()
+            elif self.pending:
+                time.sleep(max(0.0, min(0.01, self.pending[0].arrival - now)))
+        dirac_batch_synchronize(self.batch)
+        return self.results
+
+
+def graphene_requests(rate=200.0, duration=60.0, seed=1914, sizes=W.SERVE_SIZES,
+                      steps_range=(500, 5000), check_fraction=0.01):
+    """The strained-graphene request stream: Poisson arrivals, grid from `sizes`,
+    steps uniform in `steps_range`, seeded strain and packet per request."""
+    reqs = []
+    rng = np.random.default_rng(seed + 1)
+    for rid, (t, n, steps, s) in enumerate(W.serve_requests(rate, duration, seed, sizes,
+                                                            steps_range)):
+        reqs.append(Request(t, rid, (lambda n=n, steps=steps, s=s: W.serve_instance(n, steps, s)),
+                            n, n, steps, bool(rng.uniform() < check_fraction)))
+    return reqs
+
+
+def latency_summary(results: List[Result]):
+    lat = np.array([r.latency for r in results]) * 1e3
+    return {"requests": len(results), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "max_ms": float(lat.max())}
+
+
+def fp64_check(results: List[Result], stream=None):
+    """rel-L2 of each checked complex64 result against the same run in complex128."""
+    out = []
+    for r in results:
+        if r.workload is None or r.state is None:
+            continue
+        w = r.workload
+        with Simulation(w, precision=DIRAC_C128, stream=stream) as s:
+            s.set_state(w.psi0)
+            s.step(r.steps, w.dt)
+            ref = s.get_state()
+        out.append({"rid": r.rid, "n": r.nx, "steps": r.steps, "rel_l2": W.rel_l2(r.state, ref)})
+    return out

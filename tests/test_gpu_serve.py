@@ -1,0 +1,61 @@
+"""Continuous batching: requests arriving while others run are admitted as memory
+frees up, and each result equals the same simulation stepped alone."""
+import numpy as np
+import pytest
+
+import paper_1909_02894_gb300 as D
+from paper_1909_02894_gb300 import serve as S
+from paper_1909_02894_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def alone(w, steps):
+    with D.Simulation(w, precision=D.DIRAC_C64) as s:
+        t = 1024 if w.nx >= 256 else 512
+        D.dirac_set_launch(s.ctx, t, t)
+        s.set_state(w.psi0)
+        s.step(steps, w.dt)
+        return s.get_state()
+
+
+def test_served_results_equal_alone_runs():
+    D.build()
+    reqs = S.graphene_requests(rate=400.0, duration=0.05, seed=5, sizes=(64, 128, 256),
+                               steps_range=(20, 120), check_fraction=0.0)
+    assert len(reqs) >= 8
+    # room for about three 256^2 requests at a time: later arrivals must wait for memory
+    budget = 3 * D.dirac_footprint_bytes(256, 256) + D.dirac_footprint_bytes(128, 128)
+    srv = S.Server(budget, steps_per_tick=8, keep_states=True)
+    try:
+        for r in reqs:
+            srv.submit(r)
+        results = srv.run(deadline=300.0)
+    finally:
+        srv.close()
+    assert len(results) == len(reqs)
+    assert srv.max_active > 1 and srv.admitted_while_busy > 0
+    by_id = {r.rid: r for r in reqs}
+    for res in results:
+        req = by_id[res.rid]
+        ref = alone(req.make(), req.steps)
+        assert np.array_equal(res.state, ref), (res.rid, W.rel_l2(res.state, ref))
+        assert res.latency > 0
+    summ = S.latency_summary(results)
+    assert summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_fp64_check_of_served_requests():
+    D.build()
+    reqs = S.graphene_requests(rate=200.0, duration=0.03, seed=9, sizes=(128,),
+                               steps_range=(200, 300), check_fraction=1.0)
+    srv = S.Server(1 << 34, steps_per_tick=16)
+    try:
+        for r in reqs:
+            srv.submit(r)
+        results = srv.run(deadline=300.0)
+    finally:
+        srv.close()
+    checks = S.fp64_check(results)
+    assert len(checks) == len(reqs) > 0
+    assert all(c["rel_l2"] <= 1e-5 for c in checks), checks
