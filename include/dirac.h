@@ -146,6 +146,19 @@ void dirac_destroy(dirac_ctx *ctx);
  * Used by the autotuner. DIRAC_EINVAL for other values. */
 dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_pass);
 
+/* Autotuner: times every CTA shape of the x and the y pass (reps launches each, CUDA
+ * events on the context's stream, output to scratch memory so the state is unchanged),
+ * applies the fastest with dirac_set_launch and returns it in *threads_x, *threads_y.
+ * The state must be set; synchronises the stream. */
+dirac_status dirac_autotune(dirac_ctx *ctx, int reps, int *threads_x, int *threads_y);
+
+/* Test hook for failure detection: in the next dirac_step, the persistent pass's
+ * bulk-copy waits expect 16 bytes that never arrive, so each wait runs out after its
+ * bound (about 1.5 s), the kernel returns early and the next synchronising call reports
+ * DIRAC_ETIMEOUT; the context stays usable (set the state again). No effect on the
+ * other launch shapes. */
+dirac_status dirac_test_timeout_next_step(dirac_ctx *ctx);
+
 /* Number of kernel launches this context has enqueued so far (for accounting). */
 long dirac_launch_count(const dirac_ctx *ctx);
 

@@ -28,6 +28,7 @@ ABI_SYMBOLS = (
     "dirac_create", "dirac_set_state", "dirac_get_state", "dirac_step",
     "dirac_observables", "dirac_synchronize", "dirac_last_error", "dirac_destroy",
     "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc", "dirac_footprint_bytes",
+    "dirac_autotune", "dirac_test_timeout_next_step",
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
@@ -98,6 +99,10 @@ def lib():
         L.dirac_launch_count.restype = l
         L.dirac_norms_noalloc.argtypes = [vp, vp, i, i, d, d, vp, vp]
         L.dirac_norms_noalloc.restype = C.c_int
+        L.dirac_test_timeout_next_step.argtypes = [vp]
+        L.dirac_test_timeout_next_step.restype = C.c_int
+        L.dirac_autotune.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
+        L.dirac_autotune.restype = C.c_int
         L.dirac_footprint_bytes.argtypes = [C.POINTER(_Grid), i]
         L.dirac_footprint_bytes.restype = C.c_size_t
         L.dirac_batch_create.argtypes = [C.c_size_t, i, vp, i, C.POINTER(vp)]
@@ -228,6 +233,17 @@ def dirac_norms_noalloc(psi, weight, ax: float, ay: float, out, stream=None):
         wp = weight.data_ptr()
     _check(lib().dirac_norms_noalloc(psi.data_ptr(), wp, nx, ny, float(ax), float(ay),
                                      out.data_ptr(), stream), None)
+
+
+def dirac_test_timeout_next_step(ctx):
+    _check(lib().dirac_test_timeout_next_step(ctx), ctx)
+
+
+def dirac_autotune(ctx, reps: int = 20):
+    """Times every CTA shape of both passes and keeps the fastest; returns (tx, ty)."""
+    tx, ty = C.c_int(0), C.c_int(0)
+    _check(lib().dirac_autotune(ctx, int(reps), C.byref(tx), C.byref(ty)), ctx)
+    return tx.value, ty.value
 
 
 def dirac_footprint_bytes(nx: int, ny: int, precision: int = DIRAC_C64) -> int:

@@ -36,6 +36,7 @@ struct dirac_ctx {
   double dt_cached = 0.0;
   bool state_set = false;
   int threads_x = 0, threads_y = 0;
+  unsigned test_timeout_next = 0;  // test hook: next dirac_step's waits run out
   long launches = 0;
   std::string err;
   std::vector<void*> allocs;

@@ -120,6 +120,8 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   ay.out = (Q4<T>*)ctx->psi;
   ay.mult = (const Q4<T>*)ctx->mult_y;
   ay.beta = (const T*)ctx->beta2T;
+  ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
+  ctx->test_timeout_next = 0;
   for (long s = 0; s < n; ++s) {
     ax.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
     ax.u_store = nullptr;
@@ -324,6 +326,71 @@ size_t dgb_footprint_bytes(int nx, int ny, dirac_precision prec) {
   return n * per_point + per_line + 4 * sizeof(double) * 2048 + 4096;
 }
 
+// Times every CTA shape of one pass (reps launches each, CUDA events on the context's
+// stream) with its output in scratch memory, so the state is untouched; returns the
+// fastest shape (threads value for dirac_set_launch).
+template <typename T>
+static dirac_status tune_pass(dirac_ctx* ctx, int axis, int reps, int* best, float* best_ms) {
+  LinePassArgs<T> a = pass_args<T>(ctx, axis);
+  a.in = (const Q4<T>*)ctx->psi;  // any data of the pass's shape: the time does not depend on it
+  a.out = (Q4<T>*)ctx->scratch1;
+  a.mult = (const Q4<T>*)(axis == 0 ? ctx->mult_x : ctx->mult_y);
+  a.beta = (const T*)(axis == 0 ? ctx->beta1 : ctx->beta2T);
+  a.u_store = (axis == 1 && !ctx->u_identity) ? (const Q4<T>*)ctx->u2_t : nullptr;
+  const int L = a.L;
+  const int options[3] = {256, 512, 1024};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0), "tune");
+  CK(cudaEventCreate(&e1), "tune");
+  *best = 0;
+  *best_ms = 1e30f;
+  for (int t : options) {
+    if (t == 1024 && !(sizeof(T) == 4 && L >= 256)) continue;  // persistent: complex64 only
+    const int opt = t == 256 ? 0 : t == 512 ? 1 : 2;
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_line_pass<T>(a, MODE_STEP, opt, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_line_pass<T>(a, MODE_STEP, opt, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(ctx, e, "autotune");
+    }
+    ctx->launches += reps + 2;
+    if (ms < *best_ms) {
+      *best_ms = ms;
+      *best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *best_ms /= reps;
+  return DIRAC_OK;
+}
+
+template <typename T>
+static dirac_status autotune_impl(dirac_ctx* ctx, int reps, int* tx, int* ty) {
+  if (!ctx->scratch1) {
+    CK(dalloc(ctx, &ctx->scratch1, npts(ctx) * sizeof(Q4<T>)), "scratch");
+    CK(dalloc(ctx, &ctx->scratch2, npts(ctx) * sizeof(Q4<T>)), "scratch");
+  }
+  if (ctx->dt_cached == 0.0) {
+    dirac_status s = tables_for_dt<T>(ctx, 0.01);
+    if (s != DIRAC_OK) return s;
+  }
+  float mx, my;
+  dirac_status s = tune_pass<T>(ctx, 0, reps, tx, &mx);
+  if (s == DIRAC_OK) s = tune_pass<T>(ctx, 1, reps, ty, &my);
+  if (s != DIRAC_OK) return s;
+  ctx->threads_x = *tx;
+  ctx->threads_y = *ty;
+  return DIRAC_OK;
+}
+
 // ------------------------------------------------------------------------ the ABI
 extern "C" {
 
@@ -498,6 +565,20 @@ dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_
 }
 
 long dirac_launch_count(const dirac_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+dirac_status dirac_test_timeout_next_step(dirac_ctx* ctx) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  ctx->test_timeout_next = 16;
+  return DIRAC_OK;
+}
+
+dirac_status dirac_autotune(dirac_ctx* ctx, int reps, int* threads_x, int* threads_y) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (!threads_x || !threads_y || reps < 1) return fail(ctx, DIRAC_EINVAL, "bad arguments");
+  if (!ctx->state_set) return fail(ctx, DIRAC_ESTATE, "set_state must come before autotune");
+  return ctx->prec == DIRAC_C64 ? autotune_impl<float>(ctx, reps, threads_x, threads_y)
+                                : autotune_impl<double>(ctx, reps, threads_x, threads_y);
+}
 
 size_t dirac_footprint_bytes(const dirac_grid* grid, dirac_precision precision) {
   if (!grid || grid->nx <= 0 || grid->ny <= 0) return 0;

@@ -63,6 +63,8 @@ struct LinePassArgs {
   const InstPtrs<T>* inst;  // batched launch: per-instance pointers (overrides the above)
   const int* n_inst;        // batched launch: number of active instances (device memory)
   int inst_capacity;        // batched launch: table entries (host side, sizes the grid)
+  unsigned test_extra_tx;   // test hook: bytes a bulk copy never delivers (0 normally);
+                            // makes the persistent pass's bounded wait run out
 };
 
 // Batched launches: a block (or group) of lines belongs to instance `k`; take that

@@ -41,7 +41,7 @@ struct PGeo {
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 
-constexpr int kWaitTries = 1 << 22;
+constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
 constexpr int kErrTimeout = 1;
 
 template <typename T, int L>
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(1024, 1)
     size_t first;
     const LinePassArgs<T> x = args_of(grp, &first);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[slot], GROUP_BYTES);
+    mbar_arrive_expect_tx(&bars[slot], GROUP_BYTES + a0.test_extra_tx);
     bulk_copy_g2s(psi_buf[slot], x.in + first, GROUP_BYTES, &bars[slot]);
     if (x.beta) bulk_prefetch_l2(x.beta + first, BETA_BYTES);
     if (x.u_store) bulk_prefetch_l2(x.u_store + first, U_BYTES);
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(1024, 1)
     const bool has_next = s + n_clusters < n_super;
     if (!failed) {
       if (tid == 0 && has_next) issue((s + n_clusters) * CS + rank, b ^ 1);
-      const bool ok = mbar_wait_bounded(&bars[b], (it >> 1) & 1, kWaitTries);
+      const bool ok = mbar_wait_bounded(&bars[b], (it >> 1) & 1, kWaitNs);
       if (__syncthreads_or(!ok)) {
         failed = true;
         if (tid == 0) atomicExch(err, kErrTimeout);
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(1024, 1)
     // cluster has finished reading
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
   }
-  if (failed && tid == 0 && pending >= 0) mbar_wait_bounded(&bars[pending], pending_par, kWaitTries);
+  if (failed && tid == 0 && pending >= 0) mbar_wait_bounded(&bars[pending], pending_par, kWaitNs);
 }
 
 }  // namespace dgb

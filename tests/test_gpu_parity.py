@@ -218,3 +218,38 @@ def test_every_cta_shape_matches_oracle(prec, threads, nx, ny):
         s.step(4, w.dt)
         got = s.get_state()
     assert W.rel_l2(got, ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PID)
+def test_autotune_keeps_state_and_picks_a_valid_shape(prec, tmp_path):
+    from paper_1909_02894_gb300 import autotune
+
+    w = W.graphene_strained(n=512, steps=6)
+    ref = oracle_run(w, 6)
+    with D.Simulation(w, precision=prec) as s:
+        s.set_state(w.psi0)
+        tx, ty = autotune.tune(s, prec, cache_path=str(tmp_path / "cache.json"), reps=5)
+        assert tx in (256, 512, 1024) and ty in (256, 512, 1024)
+        s.step(6, w.dt)
+        assert W.rel_l2(s.get_state(), ref) <= TOL[prec]
+        assert autotune.tune(s, prec, cache_path=str(tmp_path / "cache.json")) == (tx, ty)
+
+
+def test_bounded_wait_timeout_is_reported_and_context_recovers():
+    """Failure detection without a GPU fault: a bulk-copy wait that nothing completes
+    runs out after its bound; the kernel returns, dirac_synchronize reports
+    DIRAC_ETIMEOUT, and the context works again after the state is set anew."""
+    w = W.graphene_strained(n=1024, steps=2)
+    with D.Simulation(w, precision=D.DIRAC_C64) as s:
+        D.dirac_set_launch(s.ctx, 1024, 1024)
+        s.set_state(w.psi0)
+        D.dirac_test_timeout_next_step(s.ctx)
+        s.step(1, w.dt)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_synchronize(s.ctx)
+        assert e.value.status == D.DIRAC_ETIMEOUT
+        s.set_state(w.psi0)
+        s.step(2, w.dt)
+        got = s.get_state()
+    ref = oracle_run(w, 2)
+    assert W.rel_l2(got, ref) <= TOL[D.DIRAC_C64]
