@@ -152,35 +152,47 @@ def dist_setup(args):
 
 
 def run_reference(args, wl_name):
-    """The FP64 CPU oracle, as it stands, timed on the host cores on a bounded sample."""
+    """The FP64 CPU oracle, as it stands, timed on the host cores as the reference arm.
+    Each of the K timed steps is one oracle time step on a bounded sample of the
+    workload: the same recipe on the largest grid whose K + W steps fit about two
+    minutes (estimated from a one-step probe)."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
     import oracle
 
     oracle.build()
-    w, prec, _ = workload(wl_name)
-    prob = oracle.Problem.from_workload(w)
-    pts = w.nx * w.ny
-    # per-step cost from the difference of a 2-step and a 1-step run (setup cancels)
+    w_full, prec, _ = workload(wl_name)
+    recipe = {"large-4096": lambda n: W.large_4096(n=n, steps=1),
+              "graphene-1024-c64": lambda n: W.graphene_strained(n=n, steps=1),
+              "graphene-1024-c128": lambda n: W.graphene_strained(n=n, steps=1),
+              "plain-128-c128": lambda n: W.plain_128(n=n, steps=1)}[wl_name]
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    budget_s = 120.0
+    n = 256 if w_full.nx >= 256 else w_full.nx
+    probe = recipe(n)
+    pp = oracle.Problem.from_workload(probe)
     t0 = time.perf_counter()
-    oracle.run(prob, w.psi0, w.dt, 1)
-    t1 = time.perf_counter()
-    oracle.run(prob, w.psi0, w.dt, 2)
-    t2 = time.perf_counter()
-    per_step = max((t2 - t1) - (t1 - t0), 1e-9)
-    # One timed step is one oracle time step on the full grid (a K-step run would take
-    # K times several seconds); it is measured as the difference of a 2-step and a
-    # 1-step run so that the coefficient setup cancels.
-    steps = 1
-    value = pts / per_step
+    oracle.run(pp, probe.psi0, probe.dt, 1)
+    per_pt = (time.perf_counter() - t0) / probe.points
+    while n * 2 <= w_full.nx and per_pt * (2 * n) ** 2 * 1.15 * (steps + warm) <= budget_s:
+        n *= 2
+    w = recipe(n)
+    prob = oracle.Problem.from_workload(w)
+    psi = oracle.run(prob, w.psi0, w.dt, warm) if warm else w.psi0
+    t0 = time.perf_counter()
+    oracle.run(prob, psi, w.dt, steps)
+    elapsed = time.perf_counter() - t0
+    value = w.points * steps / elapsed
+    sample = f"{steps} oracle steps on the {n}^2 grid of the {w_full.name} recipe"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "steps": steps, "warmup": warm, "ms_per_step": elapsed / steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w.name, "precision": "c128 oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
-                         "sample": f"1 and 2 full oracle steps of {w.name}, difference"},
+        "data": "synthetic", "config": {"workload": w_full.name, "precision": "f64 oracle",
+                                        "sample_grid": [n, n]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                         "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
