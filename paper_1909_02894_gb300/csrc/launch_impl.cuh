@@ -103,8 +103,8 @@ template <int L>
 static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st) {
   using PG = PGeo<float, L>;
   if (!a.err || a.n_lines % PG::GL != 0) return cudaErrorInvalidValue;
-  auto kern = line_pass_persistent<float, L>;
-  static int max_clusters[64] = {0};
+  auto kern = a.inst ? line_pass_persistent<float, L, true> : line_pass_persistent<float, L, false>;
+  static int max_clusters[2][64] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -120,7 +120,8 @@ static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st)
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (!max_clusters[dev]) {
+  int& cached = max_clusters[a.inst ? 1 : 0][dev];
+  if (!cached) {
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG::SMEM);
     if (e != cudaSuccess) return e;
     cfg.gridDim = dim3(PG::CS * 64, 1, 1);
@@ -128,10 +129,10 @@ static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st)
     e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
     if (e != cudaSuccess) return e;
     if (n <= 0) return cudaErrorInvalidConfiguration;
-    max_clusters[dev] = n;
+    cached = n;
   }
   const int groups = (a.inst ? a.inst_capacity : 1) * (a.n_lines / PG::LPI);
-  int clusters = max_clusters[dev];
+  int clusters = cached;
   if (clusters > groups / PG::CS) clusters = groups / PG::CS;
   cfg.gridDim = dim3(clusters * PG::CS, 1, 1);
   return cudaLaunchKernelEx(&cfg, kern, a, groups, a.err);

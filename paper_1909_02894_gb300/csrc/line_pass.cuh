@@ -466,7 +466,15 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
     }
   }
 
-  fft_passes<T, L, E, true>(v, buf, j, a.tw);
+  {
+    // The inverse FFT's index and twiddle-address arithmetic equals the forward one's;
+    // an opaque copy of j and buf makes the compiler recompute it instead of keeping
+    // every pass's values live across the k-space multiply (which spilled).
+    int j2 = j;
+    Cx<T>* buf2 = buf;
+    asm volatile("" : "+r"(j2), "+l"(buf2));
+    fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
+  }
 
   // ---- epilogue into the staging buffer [lcta][i] (line stride L + 1 points); thread c
   // writes component c of each point

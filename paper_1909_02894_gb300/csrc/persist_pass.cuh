@@ -44,17 +44,20 @@ struct PGeo {
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
 constexpr int kErrTimeout = 1;
 
-template <typename T, int L>
+// BATCH: the launch covers several instances (a0.inst); otherwise every pointer stays a
+// kernel parameter, which the compiler reads from the constant bank instead of keeping
+// in registers.
+template <typename T, int L, bool BATCH>
 __global__ void __launch_bounds__(1024, 1)
-    line_pass_persistent(LinePassArgs<T> a, int n_groups, int* __restrict__ err) {
+    line_pass_persistent(const LinePassArgs<T> a0, int n_groups, int* __restrict__ err) {
   using PG = PGeo<T, L>;
   using Gm = typename PG::G;
   constexpr int E = PG::E, J = L / E, LPI = PG::LPI, CS = PG::CS, GL = PG::GL;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  Cx<T>* fbuf = reinterpret_cast<Cx<T>*>(smem_raw);
-  Q4<T>* psi_buf[2] = {reinterpret_cast<Q4<T>*>(smem_raw + PG::F_BYTES),
-                       reinterpret_cast<Q4<T>*>(smem_raw + PG::F_BYTES + PG::PSI_BYTES)};
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + PG::F_BYTES + 2 * PG::PSI_BYTES);
+  extern __shared__ __align__(128) unsigned char psmem[];
+  Cx<T>* fbuf = reinterpret_cast<Cx<T>*>(psmem);
+  Q4<T>* psi_buf[2] = {reinterpret_cast<Q4<T>*>(psmem + PG::F_BYTES),
+                       reinterpret_cast<Q4<T>*>(psmem + PG::F_BYTES + PG::PSI_BYTES)};
+  uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::F_BYTES + 2 * PG::PSI_BYTES);
 
   const int tid = threadIdx.x;
   const int lcta = tid / PG::TPL;
@@ -72,20 +75,20 @@ __global__ void __launch_bounds__(1024, 1)
   const int cluster_id = blockIdx.x / CS, n_clusters = gridDim.x / CS;
 
   // batched launch: groups of instance k are [k gpi, (k + 1) gpi)
-  const int gpi = a.n_lines / LPI;
-  if (a.inst) n_groups = *a.n_inst * gpi;
+  const int gpi = a0.n_lines / LPI;
+  if constexpr (BATCH) n_groups = *a0.n_inst * gpi;
   const int n_super = n_groups / CS;
-  const LinePassArgs<T> a0 = a;
   auto args_of = [&](int grp, size_t* first) {
-    LinePassArgs<T> x = a0;
-    int lg = grp;
-    if (a0.inst) {
+    if constexpr (BATCH) {
+      LinePassArgs<T> x = a0;
       const int k = grp / gpi;
       bind_instance(x, k);
-      lg = grp - k * gpi;
+      *first = (size_t)(grp - k * gpi) * LPI * L;
+      return x;
+    } else {
+      *first = (size_t)grp * LPI * L;
+      return a0;
     }
-    *first = (size_t)lg * LPI * L;
-    return x;
   };
   auto issue = [&](int grp, int slot) {
     size_t first;
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(1024, 1)
       }
     }
     size_t gfirst;
-    a = args_of(g, &gfirst);
+    const LinePassArgs<T> a = args_of(g, &gfirst);
     if (!failed) {
       const size_t row = gfirst + (size_t)lcta * L;
       const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_buf[b] + (size_t)lcta * L) + c;
@@ -154,10 +157,16 @@ __global__ void __launch_bounds__(1024, 1)
         v[m] = {q.x * vr + ((q.y * vr - sl * vi) - sh * vi),
                 q.x * vi + ((q.y * vi + sl * vr) + sh * vr)};
       }
-      fft_passes<T, L, E, true>(v, buf, j, a.tw);
+      // The inverse FFT's index and twiddle-address arithmetic equals the forward one's;
+      // an opaque copy of j and buf makes the compiler recompute it instead of keeping
+      // every pass's values live across the k-space multiply (which spilled).
+      int j2 = j;
+      Cx<T>* buf2 = buf;
+      asm volatile("" : "+r"(j2), "+l"(buf2));
+      fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
 
       __syncthreads();  // the FFT buffer becomes the staging buffer
-      Q4<T>* stage = reinterpret_cast<Q4<T>*>(smem_raw);
+      Q4<T>* stage = reinterpret_cast<Q4<T>*>(psmem);
       Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
@@ -181,20 +190,27 @@ __global__ void __launch_bounds__(1024, 1)
     // writes rows i of its L/CS slice, reading the owners' staging buffers
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
     if (!failed) {
-      const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(smem_raw);
+      const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(psmem);
       const int line0 = (int)(gfirst / L) - rank * LPI;
       const int i0 = rank * (L / CS);
       constexpr int NIT = (L / CS) * GL / PG::THREADS;
       Q4<T> val[NIT];
+      if constexpr (CS > 1) {
+        // gather through distributed shared memory: 32-bit shared::cluster addresses
+        const uint32_t local = smem_u32(stage);
 #pragma unroll
-      for (int q = 0; q < NIT; ++q) {
-        const int itm = tid + q * PG::THREADS;
-        const int gg = itm % GL, owner = gg / LPI;
-        const Q4<T>* src = stage;
-        if constexpr (CS > 1) {
-          if (owner != rank) src = cg::this_cluster().map_shared_rank(stage, owner);
+        for (int q = 0; q < NIT; ++q) {
+          const int itm = tid + q * PG::THREADS;
+          const int gg = itm % GL, owner = gg / LPI;
+          const uint32_t off = (uint32_t)(((gg - owner * LPI) * (L + 1) + i0 + itm / GL) * sizeof(Q4<T>));
+          val[q] = ld_dsmem_q4<T>(mapa_shared(local, owner) + off);
         }
-        val[q] = src[(size_t)(gg - owner * LPI) * (L + 1) + i0 + itm / GL];
+      } else {
+#pragma unroll
+        for (int q = 0; q < NIT; ++q) {
+          const int itm = tid + q * PG::THREADS;
+          val[q] = stage[(size_t)(itm % GL) * (L + 1) + i0 + itm / GL];
+        }
       }
 #pragma unroll
       for (int q = 0; q < NIT; ++q) {
