@@ -102,7 +102,9 @@ static int sm_count() {
 template <int L>
 static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st) {
   using PG = PGeo<float, L>;
-  if (!a.err || a.n_lines % PG::GL != 0) return cudaErrorInvalidValue;
+  // one U field per pass: the U landing zone holds either the load-side or the
+  // store-side matrices (batched launches keep the same rule per instance)
+  if (!a.err || a.n_lines % PG::GL != 0 || (a.u_load && a.u_store)) return cudaErrorInvalidValue;
   auto kern = a.inst ? line_pass_persistent<float, L, true> : line_pass_persistent<float, L, false>;
   static int max_clusters[2][64] = {};
   int dev = 0;

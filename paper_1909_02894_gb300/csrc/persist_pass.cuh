@@ -1,21 +1,27 @@
 // Persistent, prefetching variant of the fused line pass (complex64 step mode).
 //
 // One 1024-thread CTA per SM loops over groups of lines, 4096 points per group (LPI =
-// 4096 / L lines). While it transforms group g, thread 0 has already started a bulk
-// asynchronous copy of group g + gridDim.x's spinor rows into the other half of a
-// double buffer in shared memory (completion counted on an mbarrier) and an L2 bulk
-// prefetch of that group's b - 1 and U rows. The FFT, k-space multiply, inverse FFT and
-// epilogue are those of line_pass_kernel (eigencomponent per thread, radix-8 passes);
-// the spinor values for the load and for the epilogue come from shared memory, so the
-// only global-memory latency left in a group's critical path is the L2 hit of its b - 1
-// and U values. The output leaves in the transposed layout as segments of LPI lines; for
-// 4096-point lines the CTAs run as clusters of 4 that gather their staged lines through
-// distributed shared memory into 4-line segments.
+// 4096 / L lines). Shared memory holds three regions: the FFT buffer (also the staging
+// buffer of the transposed store), a spinor landing zone and a b - 1 / U landing zone.
+// Thread 0 fills both landing zones with bulk asynchronous copies whose completion is
+// counted on one mbarrier each:
+//   * spinor rows of group g + 1 are requested as soon as every thread has read group g's
+//     rows (right after the load), so they arrive while group g is transformed. Each
+//     thread parks its own component of its points (needed again by the epilogue) in
+//     tensor memory, which frees the zone that early;
+//   * b - 1 and U rows of group g + 1 are requested once group g's epilogue has used the
+//     zone, and arrive during group g + 1's transforms.
+// So a group's critical path holds no global-memory load but the k-space multipliers and
+// twiddles (cached tables). The FFT, k-space multiply, inverse FFT and epilogue are those
+// of line_pass_kernel (eigencomponent per thread, radix-8 passes). The output leaves in
+// the transposed layout as segments of LPI lines; for 4096-point lines the CTAs run as
+// clusters of 4 that gather their staged lines through distributed shared memory into
+// 4-line segments.
 //
 // Every wait on an mbarrier is bounded: if one runs out, the CTA records an error code
 // in *err, stops issuing copies and transforming, keeps taking part in the cluster
 // barriers until its peers finish (so none of them waits forever), waits (bounded) for
-// the copy it issued itself and returns.
+// the copies it issued itself, frees its tensor memory and returns.
 #pragma once
 #include "line_pass.cuh"
 
@@ -35,10 +41,20 @@ struct PGeo {
   using G = Geo<T, L, LPI, E>;               // FFT buffer plan (padded, conflict-free)
   static constexpr size_t F_BYTES = ((G::SMEM + 127) / 128) * 128;
   static constexpr size_t PSI_BYTES = (size_t)LPI * L * sizeof(Q4<T>);
-  static constexpr size_t SMEM = F_BYTES + 2 * PSI_BYTES + 2 * sizeof(uint64_t);
+  static constexpr size_t BETA_BYTES = (size_t)LPI * L * sizeof(T);
+  static constexpr size_t U_BYTES = PSI_BYTES;
+  static constexpr size_t OFF_PSI = F_BYTES;
+  static constexpr size_t OFF_BETA = OFF_PSI + PSI_BYTES;
+  static constexpr size_t OFF_U = OFF_BETA + BETA_BYTES;
+  static constexpr size_t OFF_BAR = OFF_U + U_BYTES;
+  static constexpr size_t SMEM = OFF_BAR + 32;  // two mbarriers + tensor-memory address
+  // tensor memory: 8 warps share each lane quarter, 16 columns (E complex) per warp
+  static constexpr uint32_t TMEM_COLS = (THREADS / 32 / 4) * 2 * E;
   static_assert(sizeof(T) == 4, "persistent pass is complex64 only");
   static_assert(G::THREADS == THREADS, "group must fill the CTA");
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(SMEM > 227 * 1024 / 2, "one CTA per SM (the tensor-memory allocation relies on it)");
+  static_assert(TMEM_COLS == 128 && 2 * E == 16, "tensor-memory layout");
 };
 
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
@@ -46,7 +62,8 @@ constexpr int kErrTimeout = 1;
 
 // BATCH: the launch covers several instances (a0.inst); otherwise every pointer stays a
 // kernel parameter, which the compiler reads from the constant bank instead of keeping
-// in registers.
+// in registers. Each instance has at most one of u_load / u_store (the U landing zone
+// holds one matrix field).
 template <typename T, int L, bool BATCH>
 __global__ void __launch_bounds__(1024, 1)
     line_pass_persistent(const LinePassArgs<T> a0, int n_groups, int* __restrict__ err) {
@@ -55,20 +72,21 @@ __global__ void __launch_bounds__(1024, 1)
   constexpr int E = PG::E, J = L / E, LPI = PG::LPI, CS = PG::CS, GL = PG::GL;
   extern __shared__ __align__(128) unsigned char psmem[];
   Cx<T>* fbuf = reinterpret_cast<Cx<T>*>(psmem);
-  Q4<T>* psi_buf[2] = {reinterpret_cast<Q4<T>*>(psmem + PG::F_BYTES),
-                       reinterpret_cast<Q4<T>*>(psmem + PG::F_BYTES + PG::PSI_BYTES)};
-  uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::F_BYTES + 2 * PG::PSI_BYTES);
+  Q4<T>* psi_z = reinterpret_cast<Q4<T>*>(psmem + PG::OFF_PSI);
+  T* beta_z = reinterpret_cast<T*>(psmem + PG::OFF_BETA);
+  Q4<T>* u_z = reinterpret_cast<Q4<T>*>(psmem + PG::OFF_U);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::OFF_BAR);  // [0] spinor, [1] b-1/U
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(psmem + PG::OFF_BAR + 2 * sizeof(uint64_t));
 
   const int tid = threadIdx.x;
+  const int warp = tid >> 5;
   const int lcta = tid / PG::TPL;
   const int r = tid - lcta * PG::TPL;
   const int c = r & 1;
   const int j = r >> 1;
   Cx<T>* buf = fbuf + lcta * Gm::STRIDE + c * Gm::COMP;
   const T sg = c ? T(-1) : T(1);
-  constexpr uint32_t GROUP_BYTES = (uint32_t)(LPI * L * sizeof(Q4<T>));
-  constexpr uint32_t BETA_BYTES = (uint32_t)(LPI * L * sizeof(T));
-  constexpr uint32_t U_BYTES = GROUP_BYTES;
+  constexpr uint32_t GROUP_BYTES = (uint32_t)PG::PSI_BYTES;
   // cluster geometry: super-group s = lines [s GL, s GL + GL); CTA rank q owns group s CS + q
   int rank = 0;
   if constexpr (CS > 1) rank = (int)cg::this_cluster().block_rank();
@@ -90,15 +108,23 @@ __global__ void __launch_bounds__(1024, 1)
       return a0;
     }
   };
-  auto issue = [&](int grp, int slot) {
+  auto issue_psi = [&](int grp) {  // thread 0
     size_t first;
     const LinePassArgs<T> x = args_of(grp, &first);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[slot], GROUP_BYTES + a0.test_extra_tx);
-    bulk_copy_g2s(psi_buf[slot], x.in + first, GROUP_BYTES, &bars[slot]);
-    if (x.beta) bulk_prefetch_l2(x.beta + first, BETA_BYTES);
-    if (x.u_store) bulk_prefetch_l2(x.u_store + first, U_BYTES);
-    if (x.u_load) bulk_prefetch_l2(x.u_load + first, U_BYTES);
+    mbar_arrive_expect_tx(&bars[0], GROUP_BYTES + a0.test_extra_tx);
+    bulk_copy_g2s(psi_z, x.in + first, GROUP_BYTES, &bars[0]);
+  };
+  auto issue_bu = [&](int grp) {  // thread 0; an empty request completes its phase at once
+    size_t first;
+    const LinePassArgs<T> x = args_of(grp, &first);
+    const Q4<T>* usrc = x.u_load ? x.u_load : x.u_store;
+    const uint32_t bytes =
+        (x.beta ? (uint32_t)PG::BETA_BYTES : 0u) + (usrc ? (uint32_t)PG::U_BYTES : 0u);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bars[1], bytes);
+    if (x.beta) bulk_copy_g2s(beta_z, x.beta + first, (uint32_t)PG::BETA_BYTES, &bars[1]);
+    if (usrc) bulk_copy_g2s(u_z, usrc + first, (uint32_t)PG::U_BYTES, &bars[1]);
   };
 
   if (tid == 0) {
@@ -106,45 +132,68 @@ __global__ void __launch_bounds__(1024, 1)
     mbar_init(&bars[1], 1);
     fence_mbar_init();
   }
+  if (warp == 0) tmem_alloc(tslot, PG::TMEM_COLS);
+  tmem_fence_before_sync();
   __syncthreads();
-  if (tid == 0 && cluster_id < n_super) issue(cluster_id * CS + rank, 0);
+  tmem_fence_after_sync();
+  const uint32_t tbase = *tslot;
+  // this warp's parking columns: lane quarter warp % 4, column slice warp / 4
+  const uint32_t tpark =
+      tbase + ((32u * (uint32_t)(warp & 3)) << 16) + 16u * (uint32_t)(warp >> 2);
+  if (tid == 0 && cluster_id < n_super) {
+    issue_psi(cluster_id * CS + rank);
+    issue_bu(cluster_id * CS + rank);
+  }
 
-  bool failed = false;      // uniform across the CTA
-  int pending = -1;         // slot of a copy issued and not yet waited for (after a failure)
-  uint32_t pending_par = 0; // the phase parity that copy completes
+  bool failed = false;  // uniform across the CTA
+  // copies requested / phases waited for, per mbarrier (uniform; at most one outstanding)
+  const uint32_t first_issue = cluster_id < n_super ? 1u : 0u;
+  uint32_t issued[2] = {first_issue, first_issue};
+  uint32_t done[2] = {0u, 0u};
   int it = 0;
   for (int s = cluster_id; s < n_super; s += n_clusters, ++it) {
-    const int b = it & 1;
+    const uint32_t par = (uint32_t)it & 1u;
     const int g = s * CS + rank;
     const bool has_next = s + n_clusters < n_super;
-    if (!failed) {
-      if (tid == 0 && has_next) issue((s + n_clusters) * CS + rank, b ^ 1);
-      const bool ok = mbar_wait_bounded(&bars[b], (it >> 1) & 1, kWaitNs);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        if (tid == 0) atomicExch(err, kErrTimeout);
-        pending = has_next ? (b ^ 1) : -1;
-        pending_par = ((it + 1) >> 1) & 1;
-      }
-    }
     size_t gfirst;
     const LinePassArgs<T> a = args_of(g, &gfirst);
     if (!failed) {
-      const size_t row = gfirst + (size_t)lcta * L;
-      const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_buf[b] + (size_t)lcta * L) + c;
+      bool ok = mbar_wait_bounded(&bars[0], par, kWaitNs);
+      if (ok && a.u_load) ok = mbar_wait_bounded(&bars[1], par, kWaitNs);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        if (tid == 0) atomicExch(err, kErrTimeout);
+      } else {
+        done[0] += 1;
+      }
+    }
+    if (!failed) {
+      const int lrow = lcta * L;  // this line's first point within the group
+      const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_z + lrow) + c;
       Cx<T> v[E];
+      {
+        float park[2 * E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int i = j + m * J;
-        Cx<T> own = src_c[2 * i];
-        Cx<T> oth = shfl_pair(own);
-        if (a.u_load) {
-          own = apply_u_row(ldg_q4(a.u_load + row + i), own, oth, c);
-          oth = shfl_pair(own);
+        for (int m = 0; m < E; ++m) {
+          const int i = j + m * J;
+          Cx<T> own = src_c[2 * i];
+          Cx<T> oth = shfl_pair(own);
+          if (a.u_load) {
+            own = apply_u_row(u_z[lrow + i], own, oth, c);
+            oth = shfl_pair(own);
+          }
+          park[2 * m] = own.re;
+          park[2 * m + 1] = own.im;
+          const Cx<T> p1 = c ? oth : own, p2 = c ? own : oth;
+          if (a.sigma == 0) v[m] = {p1.re + sg * p2.re, p1.im + sg * p2.im};
+          else v[m] = {p1.re + sg * p2.im, p1.im - sg * p2.re};
         }
-        const Cx<T> p1 = c ? oth : own, p2 = c ? own : oth;
-        if (a.sigma == 0) v[m] = {p1.re + sg * p2.re, p1.im + sg * p2.im};
-        else v[m] = {p1.re + sg * p2.im, p1.im - sg * p2.re};
+        tmem_st16(tpark, park);
+      }
+      __syncthreads();  // the spinor zone has been read: request the next group's rows
+      if (has_next) {
+        if (tid == 0) issue_psi((s + n_clusters) * CS + rank);
+        issued[0] += 1;
       }
 
       fft_passes<T, L, E, false>(v, buf, j, a.tw);
@@ -165,30 +214,47 @@ __global__ void __launch_bounds__(1024, 1)
       asm volatile("" : "+r"(j2), "+l"(buf2));
       fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
 
-      __syncthreads();  // the FFT buffer becomes the staging buffer
-      Q4<T>* stage = reinterpret_cast<Q4<T>*>(psmem);
-      Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
+      // b - 1 / U of this group; the barrier also frees the FFT buffer for staging
+      const bool ok = mbar_wait_bounded(&bars[1], par, kWaitNs);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        if (tid == 0) atomicExch(err, kErrTimeout);
+      } else {
+        done[1] += 1;
+        tmem_wait_st();
+        Q4<T>* stage = reinterpret_cast<Q4<T>*>(psmem);
+        Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
 #pragma unroll
-      for (int m = 0; m < E; ++m) {
-        if ((m & 3) == 0) asm volatile("" ::: "memory");
-        const int i = j + m * J;
-        const size_t gi = row + i;
-        const Cx<T> oth = shfl_pair(v[m]);
-        const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
-        Cx<T> d;
-        if (c == 0) d = cadd(dp, dm);
-        else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
-        Cx<T> p = src_c[2 * i];
-        if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
-        const T bm1 = a.beta ? a.beta[gi] : T(0);
-        Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
-        if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
-        my_stage[2 * i] = o;
+        for (int h = 0; h < 2; ++h) {
+          float pk[E];
+          tmem_ld8(tpark + (uint32_t)(h * E), pk);
+          tmem_wait_ld();
+#pragma unroll
+          for (int mm = 0; mm < E / 2; ++mm) {
+            const int m = h * (E / 2) + mm;
+            const int i = j + m * J;
+            const Cx<T> oth = shfl_pair(v[m]);
+            const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
+            Cx<T> d;
+            if (c == 0) d = cadd(dp, dm);
+            else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+            const Cx<T> p = {pk[2 * mm], pk[2 * mm + 1]};
+            const T bm1 = a.beta ? beta_z[lrow + i] : T(0);
+            Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+            if (a.u_store) o = apply_u_row(u_z[lrow + i], o, shfl_pair(o), c);
+            my_stage[2 * i] = o;
+          }
+        }
       }
     }
     // ---- transposed store of the super-group: out[i][s GL .. s GL + GL); CTA rank q
-    // writes rows i of its L/CS slice, reading the owners' staging buffers
+    // writes rows i of its L/CS slice, reading the owners' staging buffers. The barrier
+    // publishes the staging writes and tells thread 0 that the b - 1 / U zone is free.
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    if (!failed && has_next) {
+      if (tid == 0) issue_bu((s + n_clusters) * CS + rank);
+      issued[1] += 1;
+    }
     if (!failed) {
       const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(psmem);
       const int line0 = (int)(gfirst / L) - rank * LPI;
@@ -202,7 +268,8 @@ __global__ void __launch_bounds__(1024, 1)
         for (int q = 0; q < NIT; ++q) {
           const int itm = tid + q * PG::THREADS;
           const int gg = itm % GL, owner = gg / LPI;
-          const uint32_t off = (uint32_t)(((gg - owner * LPI) * (L + 1) + i0 + itm / GL) * sizeof(Q4<T>));
+          const uint32_t off =
+              (uint32_t)(((gg - owner * LPI) * (L + 1) + i0 + itm / GL) * sizeof(Q4<T>));
           val[q] = ld_dsmem_q4<T>(mapa_shared(local, owner) + off);
         }
       } else {
@@ -218,11 +285,21 @@ __global__ void __launch_bounds__(1024, 1)
         a.out[(size_t)(i0 + itm / GL) * a.n_lines + line0 + itm % GL] = val[q];
       }
     }
-    // staging and psi_buf[b] are free for the next super-group once every CTA of the
-    // cluster has finished reading
-    if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
+    // the staging buffer is free for the next super-group once every CTA of the cluster
+    // has read it (the loads have returned: the stores above consumed them), so the
+    // arrive needs no release fence for the outstanding global stores
+    if constexpr (CS > 1) cluster_sync_relaxed(); else __syncthreads();
   }
-  if (failed && tid == 0 && pending >= 0) mbar_wait_bounded(&bars[pending], pending_par, kWaitNs);
+  if (failed && tid == 0) {
+    // at most one copy per mbarrier is outstanding: the last one requested
+    for (int b = 0; b < 2; ++b)
+      if (issued[b] > done[b]) mbar_wait_bounded(&bars[b], (issued[b] - 1u) & 1u, kWaitNs);
+  }
+  tmem_wait_st();
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(tbase, PG::TMEM_COLS);
 }
 
 }  // namespace dgb
