@@ -39,7 +39,14 @@ struct PGeo {
   static constexpr int CS = L == 4096 ? 4 : 1;
   static constexpr int GL = LPI * CS;               // lines per output segment
   using G = Geo<T, L, LPI, E>;               // FFT buffer plan (padded, conflict-free)
-  static constexpr size_t F_BYTES = ((G::SMEM + 127) / 128) * 128;
+  // 4096-point lines run the digit-swap FFT (fft4096_swap): unpadded component buffers,
+  // which also hold the staging buffer of L + 1 points
+  static constexpr bool SWAP = L == 4096;
+  static constexpr size_t F_RAW =
+      SWAP ? ((size_t)2 * L * sizeof(Cx<T>) > (size_t)(L + 1) * sizeof(Q4<T>)
+                  ? (size_t)2 * L * sizeof(Cx<T>) : (size_t)(L + 1) * sizeof(Q4<T>))
+           : G::SMEM;
+  static constexpr size_t F_BYTES = ((F_RAW + 127) / 128) * 128;
   static constexpr size_t PSI_BYTES = (size_t)LPI * L * sizeof(Q4<T>);
   static constexpr size_t BETA_BYTES = (size_t)LPI * L * sizeof(T);
   static constexpr size_t U_BYTES = PSI_BYTES;
@@ -48,17 +55,119 @@ struct PGeo {
   static constexpr size_t OFF_U = OFF_BETA + BETA_BYTES;
   static constexpr size_t OFF_BAR = OFF_U + U_BYTES;
   static constexpr size_t SMEM = OFF_BAR + 32;  // two mbarriers + tensor-memory address
-  // tensor memory: 8 warps share each lane quarter, 16 columns (E complex) per warp
-  static constexpr uint32_t TMEM_COLS = (THREADS / 32 / 4) * 2 * E;
+  // tensor memory: 8 warps share each lane quarter; per warp slice s = warp / 4 the
+  // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds two
+  // exchange regions of 128 columns and 16 twiddle columns per slice
+  static constexpr uint32_t T_PARK = 0, T_XF = 128, T_XI = 256, T_TW = 384;
+  static constexpr uint32_t TMEM_COLS = SWAP ? 512 : 128;
   static_assert(sizeof(T) == 4, "persistent pass is complex64 only");
   static_assert(G::THREADS == THREADS, "group must fill the CTA");
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
   static_assert(SMEM > 227 * 1024 / 2, "one CTA per SM (the tensor-memory allocation relies on it)");
-  static_assert(TMEM_COLS == 128 && 2 * E == 16, "tensor-memory layout");
+  static_assert(THREADS / 32 / 4 * 2 * E == 128, "tensor-memory layout");
 };
 
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
 constexpr int kErrTimeout = 1;
+
+// ---- digit-swap FFT of 4096 points (forward, or inverse without the 1/N scale)
+//
+// Index n = d0 + 8 d1 + 64 d2 + 512 d3 (octal digits). Thread j (512 per component line)
+// holds 8 elements in registers; its index j = 16 w + lane / 2 puts j's top three bits in
+// the warp slice w / 4, the set of warps that share a tensor-memory lane quarter. The
+// transform is a radix-8 decimation in frequency (four passes over d3, d2, d1, d0, each
+// followed by the twiddles W_4096^(n' k0), W_512^(n'' k1), W_64^(d0 k2)); between passes
+// the digit in registers trades places with a digit spread over the threads:
+//   pass 1 (registers d3)  --tensor memory: registers <-> slice digit--
+//   pass 2 (d2)            --shared memory: a general permutation--
+//   pass 3 (d1)            --tensor memory--
+//   pass 4 (d0)
+// Input and output are both in natural order, element r of thread j at index j + 512 r,
+// so only one of the three exchanges goes through shared memory.
+__device__ __forceinline__ int swz4096(int idx) {
+  // XOR of index bits 6, 9, 10, 11 into bits 0..3: the write pattern (lanes vary bits
+  // 0..3) and the read pattern (lanes vary bits 6, 9..11) are both bank-conflict free
+  return idx ^ (((idx >> 6) & 1) | (((idx >> 9) & 7) << 1));
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void twiddle8(Cx<T> (&v)[8], Cx<T> w1, Cx<T> w2, Cx<T> w4) {
+  // v[t] *= w^t (conjugate for the inverse); w^3, w^5, w^6, w^7 as products of the three
+  // table values (at most two extra roundings)
+  const Cx<T> w3 = cmul(w1, w2);
+  const Cx<T> w[8] = {w1, w1, w2, w3, w4, cmul(w4, w1), cmul(w4, w2), cmul(w4, w3)};
+#pragma unroll
+  for (int t = 1; t < 8; ++t) v[t] = INV ? cmulc(v[t], w[t]) : cmul(v[t], w[t]);
+}
+
+// registers <-> slice digit through tensor memory: thread (j mod 64, slice s) stores its
+// 8 elements at columns x + 16 s + 2 r and reads element s of every slice's block;
+// afterwards element r' comes from slice r'. `x` carries this warp's lane quarter.
+template <typename T>
+__device__ __forceinline__ void tmem_swap(Cx<T> (&v)[8], uint32_t x, int s, int q) {
+  {
+    float f[16];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      f[2 * r] = v[r].re;
+      f[2 * r + 1] = v[r].im;
+    }
+    tmem_st16(x + 16u * (uint32_t)s, f);
+  }
+  tmem_wait_st();
+  tmem_fence_before_sync();
+  named_barrier(1 + q, 256);  // the 8 warps of this lane quarter
+  tmem_fence_after_sync();
+  float g[16];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    float h[2];
+    tmem_ld2(x + 16u * (uint32_t)r + 2u * (uint32_t)s, h);
+    g[2 * r] = h[0];
+    g[2 * r + 1] = h[1];
+  }
+  tmem_wait_ld_regs(g);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = {g[2 * r], g[2 * r + 1]};
+}
+
+// tws: this thread's passes-1/2 twiddles parked in tensor memory (w, w^2, w^4 of each);
+// x: the exchange region; fc: this component's 4096-point shared buffer; tw: the pass
+// table (pass 3's twiddles depend on the slice only: one cached line per warp).
+template <typename T, bool INV>
+__device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int j, int s, int q,
+                                             uint32_t tws, uint32_t x, const Cx<T>* tw) {
+  {
+    float t1[8];
+    tmem_ld8(tws, t1);
+    dft8<T, INV>(v);
+    tmem_wait_ld_regs(t1);
+    twiddle8<T, INV>(v, {t1[0], t1[1]}, {t1[2], t1[3]}, {t1[4], t1[5]});
+  }
+  tmem_swap(v, x, s, q);
+  {
+    float t2[8];
+    tmem_ld8(tws + 8u, t2);
+    dft8<T, INV>(v);
+    tmem_wait_ld_regs(t2);
+    twiddle8<T, INV>(v, {t2[0], t2[1]}, {t2[2], t2[3]}, {t2[4], t2[5]});
+  }
+  // registers k1, threads (d0, d1, k0)  ->  registers d1, threads (k0, k1, d0)
+  const int lo = j & 7, mid = (j >> 3) & 7, hi = j >> 6;
+  __syncthreads();  // earlier readers of the buffer are done
+#pragma unroll
+  for (int r = 0; r < 8; ++r) fc[swz4096(hi * 512 + r * 64 + mid * 8 + lo)] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = fc[swz4096(lo * 512 + mid * 64 + r * 8 + hi)];
+  dft8<T, INV>(v);
+  {
+    const Cx<T>* t3 = tw + tw_offset(8, 8) + hi;  // block of span 8: [(t - 1) 8 + k]
+    twiddle8<T, INV>(v, ldg_cx(t3), ldg_cx(t3 + 8), ldg_cx(t3 + 24));
+  }
+  tmem_swap(v, x, s, q);
+  dft8<T, INV>(v);
+}
 
 // BATCH: the launch covers several instances (a0.inst); otherwise every pointer stays a
 // kernel parameter, which the compiler reads from the constant bank instead of keeping
@@ -137,9 +246,22 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tbase = *tslot;
-  // this warp's parking columns: lane quarter warp % 4, column slice warp / 4
-  const uint32_t tpark =
-      tbase + ((32u * (uint32_t)(warp & 3)) << 16) + 16u * (uint32_t)(warp >> 2);
+  const int quarter = warp & 3, slice = warp >> 2;
+  const uint32_t tlane = tbase + ((32u * (uint32_t)quarter) << 16);  // this warp's lanes
+  const uint32_t tpark = tlane + PG::T_PARK + 16u * (uint32_t)slice;
+  if constexpr (PG::SWAP) {
+    // passes 1 and 2 of the digit-swap FFT: W_4096^(j t) and W_512^((j mod 64) t) for
+    // t = 1, 2, 4, from the pass table's blocks of span 512 and 64
+    const Cx<T>* b1 = a0.tw + tw_offset(512, 8) + j;
+    const Cx<T>* b2 = a0.tw + tw_offset(64, 8) + (j & 63);
+    const Cx<T> w1 = ldg_cx(b1), w2 = ldg_cx(b1 + 512), w4 = ldg_cx(b1 + 3 * 512);
+    const Cx<T> u1 = ldg_cx(b2), u2 = ldg_cx(b2 + 64), u4 = ldg_cx(b2 + 3 * 64);
+    const float f1[8] = {w1.re, w1.im, w2.re, w2.im, w4.re, w4.im, 0.f, 0.f};
+    const float f2[8] = {u1.re, u1.im, u2.re, u2.im, u4.re, u4.im, 0.f, 0.f};
+    tmem_st8(tlane + PG::T_TW + 16u * (uint32_t)slice, f1);
+    tmem_st8(tlane + PG::T_TW + 16u * (uint32_t)slice + 8u, f2);
+    tmem_wait_st();
+  }
   if (tid == 0 && cluster_id < n_super) {
     issue_psi(cluster_id * CS + rank);
     issue_bu(cluster_id * CS + rank);
@@ -196,7 +318,11 @@ __global__ void __launch_bounds__(1024, 1)
         issued[0] += 1;
       }
 
-      fft_passes<T, L, E, false>(v, buf, j, a.tw);
+      if constexpr (PG::SWAP)
+        fft4096_swap<T, false>(v, fbuf + c * L, j, slice, quarter,
+                               tlane + PG::T_TW + 16u * (uint32_t)slice, tlane + PG::T_XF, a.tw);
+      else
+        fft_passes<T, L, E, false>(v, buf, j, a.tw);
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         if ((m & 3) == 0) asm volatile("" ::: "memory");
@@ -212,7 +338,11 @@ __global__ void __launch_bounds__(1024, 1)
       int j2 = j;
       Cx<T>* buf2 = buf;
       asm volatile("" : "+r"(j2), "+l"(buf2));
-      fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
+      if constexpr (PG::SWAP)
+        fft4096_swap<T, true>(v, fbuf + c * L, j2, slice, quarter,
+                              tlane + PG::T_TW + 16u * (uint32_t)slice, tlane + PG::T_XI, a.tw);
+      else
+        fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
 
       // b - 1 / U of this group; the barrier also frees the FFT buffer for staging
       const bool ok = mbar_wait_bounded(&bars[1], par, kWaitNs);
@@ -228,7 +358,7 @@ __global__ void __launch_bounds__(1024, 1)
         for (int h = 0; h < 2; ++h) {
           float pk[E];
           tmem_ld8(tpark + (uint32_t)(h * E), pk);
-          tmem_wait_ld();
+          tmem_wait_ld_regs(pk);
 #pragma unroll
           for (int mm = 0; mm < E / 2; ++mm) {
             const int m = h * (E / 2) + mm;
