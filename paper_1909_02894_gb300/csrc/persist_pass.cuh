@@ -56,9 +56,9 @@ struct PGeo {
   static constexpr size_t OFF_BAR = OFF_U + U_BYTES;
   static constexpr size_t SMEM = OFF_BAR + 32;  // two mbarriers + tensor-memory address
   // tensor memory: 8 warps share each lane quarter; per warp slice s = warp / 4 the
-  // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds two
-  // exchange regions of 128 columns and 16 twiddle columns per slice
-  static constexpr uint32_t T_PARK = 0, T_XF = 128, T_XI = 256, T_TW = 384;
+  // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds an
+  // exchange region of 128 columns and 32 twiddle columns per slice
+  static constexpr uint32_t T_PARK = 0, T_X = 128, T_TW = 256;
   static constexpr uint32_t TMEM_COLS = SWAP ? 512 : 128;
   static_assert(sizeof(T) == 4, "persistent pass is complex64 only");
   static_assert(G::THREADS == THREADS, "group must fill the CTA");
@@ -84,20 +84,22 @@ constexpr int kErrTimeout = 1;
 //   pass 4 (d0)
 // Input and output are both in natural order, element r of thread j at index j + 512 r,
 // so only one of the three exchanges goes through shared memory.
-__device__ __forceinline__ int swz4096(int idx) {
-  // XOR of index bits 6, 9, 10, 11 into bits 0..3: the write pattern (lanes vary bits
-  // 0..3) and the read pattern (lanes vary bits 6, 9..11) are both bank-conflict free
-  return idx ^ (((idx >> 6) & 1) | (((idx >> 9) & 7) << 1));
+// Shared-memory slot of element idx of component c: XOR of index bits 6, 9, 10, 11 into
+// bits 0..3, and of 9 for the second component. 8-byte accesses are served per half-warp
+// (8 points x 2 components); the write pattern (lanes vary bits 0..2 and c) and the read
+// pattern (bits 9..11 and c) then reach 16 different bank pairs.
+__device__ __forceinline__ int swz4096(int idx, int cx) {
+  return idx ^ (((idx >> 6) & 1) | (((idx >> 9) & 7) << 1)) ^ cx;
 }
 
+// v[t] *= w^t for t = 1..7 (conjugate for the inverse), w^t = (f[2t - 2], f[2t - 1])
 template <typename T, bool INV>
-__device__ __forceinline__ void twiddle8(Cx<T> (&v)[8], Cx<T> w1, Cx<T> w2, Cx<T> w4) {
-  // v[t] *= w^t (conjugate for the inverse); w^3, w^5, w^6, w^7 as products of the three
-  // table values (at most two extra roundings)
-  const Cx<T> w3 = cmul(w1, w2);
-  const Cx<T> w[8] = {w1, w1, w2, w3, w4, cmul(w4, w1), cmul(w4, w2), cmul(w4, w3)};
+__device__ __forceinline__ void twiddle8(Cx<T> (&v)[8], const float (&f)[16]) {
 #pragma unroll
-  for (int t = 1; t < 8; ++t) v[t] = INV ? cmulc(v[t], w[t]) : cmul(v[t], w[t]);
+  for (int t = 1; t < 8; ++t) {
+    const Cx<T> w = {f[2 * t - 2], f[2 * t - 1]};
+    v[t] = INV ? cmulc(v[t], w) : cmul(v[t], w);
+  }
 }
 
 // registers <-> slice digit through tensor memory: thread (j mod 64, slice s) stores its
@@ -131,39 +133,58 @@ __device__ __forceinline__ void tmem_swap(Cx<T> (&v)[8], uint32_t x, int s, int 
   for (int r = 0; r < 8; ++r) v[r] = {g[2 * r], g[2 * r + 1]};
 }
 
-// tws: this thread's passes-1/2 twiddles parked in tensor memory (w, w^2, w^4 of each);
-// x: the exchange region; fc: this component's 4096-point shared buffer; tw: the pass
-// table (pass 3's twiddles depend on the slice only: one cached line per warp).
+// tws: this thread's pass-1 and pass-2 twiddles parked in tensor memory (w^1..w^7 of
+// each, 16 columns apart); x: the exchange region; fc: this component's 4096-point shared
+// buffer and cx its slot XOR (0 or 9, see swz4096); tw: the pass table (pass 3's twiddles
+// depend on the slice only: one cached line per warp).
 template <typename T, bool INV>
-__device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int j, int s, int q,
-                                             uint32_t tws, uint32_t x, const Cx<T>* tw) {
+__device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, int j, int s,
+                                             int q, uint32_t tws, uint32_t x,
+                                             const Cx<T>* tw) {
   {
-    float t1[8];
-    tmem_ld8(tws, t1);
+    float t1[16];
+    tmem_ld16(tws, t1);
     dft8<T, INV>(v);
     tmem_wait_ld_regs(t1);
-    twiddle8<T, INV>(v, {t1[0], t1[1]}, {t1[2], t1[3]}, {t1[4], t1[5]});
+    twiddle8<T, INV>(v, t1);
   }
   tmem_swap(v, x, s, q);
   {
-    float t2[8];
-    tmem_ld8(tws + 8u, t2);
+    float t2[16];
+    tmem_ld16(tws + 16u, t2);
     dft8<T, INV>(v);
     tmem_wait_ld_regs(t2);
-    twiddle8<T, INV>(v, {t2[0], t2[1]}, {t2[2], t2[3]}, {t2[4], t2[5]});
+    twiddle8<T, INV>(v, t2);
   }
-  // registers k1, threads (d0, d1, k0)  ->  registers d1, threads (k0, k1, d0)
+  // registers k1, threads (d0, d1, k0)  ->  registers d1, threads (k0, k1, d0). The
+  // swizzle of the written slots depends on r only through bit 0 (index bit 6) and that
+  // of the read slots not at all, so both reduce to two bases and constant offsets:
+  //   write r: swz(hi 512 + mid 8 + lo + 64 r) = wb[r & 1] + 64 r
+  //   read r:  swz(lo 512 + mid 64 + hi + 8 r)  = rb[r & 1] + 8 r
   const int lo = j & 7, mid = (j >> 3) & 7, hi = j >> 6;
+  const int wb0 = ((hi * 512 + mid * 8 + lo) ^ (hi << 1)) ^ cx, wb1 = wb0 ^ 1;
+  const int m = ((mid & 1) | (lo << 1)) ^ cx;  // XOR applied to every read slot
+  const int rbase = (lo * 512 + mid * 64 + hi) ^ (m & 7);
+  const int m3 = (m >> 3) & 1;  // flips bit 3, the low bit of r's field
+  const int rb0 = rbase + 8 * m3, rb1 = rbase - 8 * m3;
   __syncthreads();  // earlier readers of the buffer are done
 #pragma unroll
-  for (int r = 0; r < 8; ++r) fc[swz4096(hi * 512 + r * 64 + mid * 8 + lo)] = v[r];
+  for (int r = 0; r < 8; ++r) fc[(r & 1 ? wb1 : wb0) + 64 * r] = v[r];
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = fc[swz4096(lo * 512 + mid * 64 + r * 8 + hi)];
+  for (int r = 0; r < 8; ++r) v[r] = fc[(r & 1 ? rb1 : rb0) + 8 * r];
   dft8<T, INV>(v);
   {
     const Cx<T>* t3 = tw + tw_offset(8, 8) + hi;  // block of span 8: [(t - 1) 8 + k]
-    twiddle8<T, INV>(v, ldg_cx(t3), ldg_cx(t3 + 8), ldg_cx(t3 + 24));
+    float f[16];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) {
+      const Cx<T> w = ldg_cx(t3 + 8 * (t - 1));
+      f[2 * t - 2] = w.re;
+      f[2 * t - 1] = w.im;
+    }
+    f[14] = f[15] = 0.f;
+    twiddle8<T, INV>(v, f);
   }
   tmem_swap(v, x, s, q);
   dft8<T, INV>(v);
@@ -251,15 +272,21 @@ __global__ void __launch_bounds__(1024, 1)
   const uint32_t tpark = tlane + PG::T_PARK + 16u * (uint32_t)slice;
   if constexpr (PG::SWAP) {
     // passes 1 and 2 of the digit-swap FFT: W_4096^(j t) and W_512^((j mod 64) t) for
-    // t = 1, 2, 4, from the pass table's blocks of span 512 and 64
-    const Cx<T>* b1 = a0.tw + tw_offset(512, 8) + j;
-    const Cx<T>* b2 = a0.tw + tw_offset(64, 8) + (j & 63);
-    const Cx<T> w1 = ldg_cx(b1), w2 = ldg_cx(b1 + 512), w4 = ldg_cx(b1 + 3 * 512);
-    const Cx<T> u1 = ldg_cx(b2), u2 = ldg_cx(b2 + 64), u4 = ldg_cx(b2 + 3 * 64);
-    const float f1[8] = {w1.re, w1.im, w2.re, w2.im, w4.re, w4.im, 0.f, 0.f};
-    const float f2[8] = {u1.re, u1.im, u2.re, u2.im, u4.re, u4.im, 0.f, 0.f};
-    tmem_st8(tlane + PG::T_TW + 16u * (uint32_t)slice, f1);
-    tmem_st8(tlane + PG::T_TW + 16u * (uint32_t)slice + 8u, f2);
+    // t = 1..7, from the pass table's blocks of span 512 and 64
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const Cx<T>* b = p == 0 ? a0.tw + tw_offset(512, 8) + j : a0.tw + tw_offset(64, 8) + (j & 63);
+      const int span = p == 0 ? 512 : 64;
+      float f[16];
+#pragma unroll
+      for (int t = 1; t < 8; ++t) {
+        const Cx<T> w = ldg_cx(b + (t - 1) * span);
+        f[2 * t - 2] = w.re;
+        f[2 * t - 1] = w.im;
+      }
+      f[14] = f[15] = 0.f;
+      tmem_st16(tlane + PG::T_TW + 32u * (uint32_t)slice + 16u * (uint32_t)p, f);
+    }
     tmem_wait_st();
   }
   if (tid == 0 && cluster_id < n_super) {
@@ -319,8 +346,8 @@ __global__ void __launch_bounds__(1024, 1)
       }
 
       if constexpr (PG::SWAP)
-        fft4096_swap<T, false>(v, fbuf + c * L, j, slice, quarter,
-                               tlane + PG::T_TW + 16u * (uint32_t)slice, tlane + PG::T_XF, a.tw);
+        fft4096_swap<T, false>(v, fbuf + c * L, 9 * c, j, slice, quarter,
+                               tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X, a.tw);
       else
         fft_passes<T, L, E, false>(v, buf, j, a.tw);
 #pragma unroll
@@ -338,9 +365,15 @@ __global__ void __launch_bounds__(1024, 1)
       int j2 = j;
       Cx<T>* buf2 = buf;
       asm volatile("" : "+r"(j2), "+l"(buf2));
-      if constexpr (PG::SWAP)
-        fft4096_swap<T, true>(v, fbuf + c * L, j2, slice, quarter,
-                              tlane + PG::T_TW + 16u * (uint32_t)slice, tlane + PG::T_XI, a.tw);
+      if constexpr (PG::SWAP) {
+        // the forward FFT's last exchange has been read by the whole lane quarter before
+        // the inverse FFT's first one overwrites the region
+        tmem_fence_before_sync();
+        named_barrier(1 + quarter, 256);
+        tmem_fence_after_sync();
+        fft4096_swap<T, true>(v, fbuf + c * L, 9 * c, j2, slice, quarter,
+                              tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X, a.tw);
+      }
       else
         fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
 
