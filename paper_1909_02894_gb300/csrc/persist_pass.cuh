@@ -167,7 +167,8 @@ __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, i
   const int rbase = (lo * 512 + mid * 64 + hi) ^ (m & 7);
   const int m3 = (m >> 3) & 1;  // flips bit 3, the low bit of r's field
   const int rb0 = rbase + 8 * m3, rb1 = rbase - 8 * m3;
-  __syncthreads();  // earlier readers of the buffer are done
+  // earlier readers of the buffer finished before a barrier the caller has passed: the
+  // previous group's gather (cluster barrier) or the forward FFT (barrier between FFTs)
 #pragma unroll
   for (int r = 0; r < 8; ++r) fc[(r & 1 ? wb1 : wb0) + 64 * r] = v[r];
   __syncthreads();
@@ -306,20 +307,14 @@ __global__ void __launch_bounds__(1024, 1)
     const bool has_next = s + n_clusters < n_super;
     size_t gfirst;
     const LinePassArgs<T> a = args_of(g, &gfirst);
+    Cx<T> v[E];
+    const int lrow = lcta * L;  // this line's first point within the group
     if (!failed) {
+      // a thread whose wait ran out reads whatever the zone holds; the barrier after the
+      // load turns it into a failure of the whole CTA before anything is used
       bool ok = mbar_wait_bounded(&bars[0], par, kWaitNs);
       if (ok && a.u_load) ok = mbar_wait_bounded(&bars[1], par, kWaitNs);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        if (tid == 0) atomicExch(err, kErrTimeout);
-      } else {
-        done[0] += 1;
-      }
-    }
-    if (!failed) {
-      const int lrow = lcta * L;  // this line's first point within the group
       const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_z + lrow) + c;
-      Cx<T> v[E];
       {
         float park[2 * E];
 #pragma unroll
@@ -339,12 +334,19 @@ __global__ void __launch_bounds__(1024, 1)
         }
         tmem_st16(tpark, park);
       }
-      __syncthreads();  // the spinor zone has been read: request the next group's rows
-      if (has_next) {
-        if (tid == 0) issue_psi((s + n_clusters) * CS + rank);
-        issued[0] += 1;
+      // the spinor zone has been read: request the next group's rows
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        if (tid == 0) atomicExch(err, kErrTimeout);
+      } else {
+        done[0] += 1;
+        if (has_next) {
+          if (tid == 0) issue_psi((s + n_clusters) * CS + rank);
+          issued[0] += 1;
+        }
       }
-
+    }
+    if (!failed) {
       if constexpr (PG::SWAP)
         fft4096_swap<T, false>(v, fbuf + c * L, 9 * c, j, slice, quarter,
                                tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X, a.tw);
@@ -366,10 +368,10 @@ __global__ void __launch_bounds__(1024, 1)
       Cx<T>* buf2 = buf;
       asm volatile("" : "+r"(j2), "+l"(buf2));
       if constexpr (PG::SWAP) {
-        // the forward FFT's last exchange has been read by the whole lane quarter before
-        // the inverse FFT's first one overwrites the region
+        // the forward FFT's exchanges (tensor memory and shared memory) have been read by
+        // every thread before the inverse FFT's overwrite them
         tmem_fence_before_sync();
-        named_barrier(1 + quarter, 256);
+        __syncthreads();
         tmem_fence_after_sync();
         fft4096_swap<T, true>(v, fbuf + c * L, 9 * c, j2, slice, quarter,
                               tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X, a.tw);
