@@ -42,18 +42,27 @@ struct PGeo {
   // 4096-point lines run the digit-swap FFT (fft4096_swap): unpadded component buffers,
   // which also hold the staging buffer of L + 1 points
   static constexpr bool SWAP = L == 4096;
+  // The 4096-point path pads its staging buffer and its b - 1 / U zones after every 512
+  // points (1 point, 4 floats, 1 matrix), so that the two threads of a point pair, which
+  // work on points 512 k apart in the epilogue, reach different banks.
+  static constexpr int PAD_EVERY = 512;
+  static constexpr size_t STAGE_POINTS = SWAP ? L + L / PAD_EVERY : L + 1;
   static constexpr size_t F_RAW =
-      SWAP ? ((size_t)2 * L * sizeof(Cx<T>) > (size_t)(L + 1) * sizeof(Q4<T>)
-                  ? (size_t)2 * L * sizeof(Cx<T>) : (size_t)(L + 1) * sizeof(Q4<T>))
+      SWAP ? ((size_t)2 * L * sizeof(Cx<T>) > STAGE_POINTS * sizeof(Q4<T>)
+                  ? (size_t)2 * L * sizeof(Cx<T>) : STAGE_POINTS * sizeof(Q4<T>))
            : G::SMEM;
   static constexpr size_t F_BYTES = ((F_RAW + 127) / 128) * 128;
   static constexpr size_t PSI_BYTES = (size_t)LPI * L * sizeof(Q4<T>);
   static constexpr size_t BETA_BYTES = (size_t)LPI * L * sizeof(T);
   static constexpr size_t U_BYTES = PSI_BYTES;
+  static constexpr int CHUNKS = SWAP ? L / PAD_EVERY : 1;  // bulk copies per b - 1 / U row
+  static constexpr size_t BETA_CHUNK = BETA_BYTES / CHUNKS, U_CHUNK = U_BYTES / CHUNKS;
+  static constexpr size_t BETA_PITCH = BETA_CHUNK + (SWAP ? 4 * sizeof(T) : 0);
+  static constexpr size_t U_PITCH = U_CHUNK + (SWAP ? sizeof(Q4<T>) : 0);
   static constexpr size_t OFF_PSI = F_BYTES;
   static constexpr size_t OFF_BETA = OFF_PSI + PSI_BYTES;
-  static constexpr size_t OFF_U = OFF_BETA + BETA_BYTES;
-  static constexpr size_t OFF_BAR = OFF_U + U_BYTES;
+  static constexpr size_t OFF_U = OFF_BETA + CHUNKS * BETA_PITCH;
+  static constexpr size_t OFF_BAR = OFF_U + CHUNKS * U_PITCH;
   static constexpr size_t SMEM = OFF_BAR + 32;  // two mbarriers + tensor-memory address
   // tensor memory: 8 warps share each lane quarter; per warp slice s = warp / 4 the
   // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds an
@@ -65,6 +74,11 @@ struct PGeo {
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
   static_assert(SMEM > 227 * 1024 / 2, "one CTA per SM (the tensor-memory allocation relies on it)");
   static_assert(THREADS / 32 / 4 * 2 * E == 128, "tensor-memory layout");
+  static_assert(BETA_PITCH % 16 == 0 && U_PITCH % 16 == 0 && OFF_BAR % 16 == 0, "bulk copy");
+  // positions in the padded staging buffer / b - 1 zone / U zone of point i of a line
+  static __device__ __forceinline__ int spos(int i) { return SWAP ? i + i / PAD_EVERY : i; }
+  static __device__ __forceinline__ int bpos(int i) { return SWAP ? i + 4 * (i / PAD_EVERY) : i; }
+  static __device__ __forceinline__ int upos(int i) { return SWAP ? i + i / PAD_EVERY : i; }
 };
 
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
@@ -254,8 +268,17 @@ __global__ void __launch_bounds__(1024, 1)
         (x.beta ? (uint32_t)PG::BETA_BYTES : 0u) + (usrc ? (uint32_t)PG::U_BYTES : 0u);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bars[1], bytes);
-    if (x.beta) bulk_copy_g2s(beta_z, x.beta + first, (uint32_t)PG::BETA_BYTES, &bars[1]);
-    if (usrc) bulk_copy_g2s(u_z, usrc + first, (uint32_t)PG::U_BYTES, &bars[1]);
+#pragma unroll
+    for (int k = 0; k < PG::CHUNKS; ++k) {
+      if (x.beta)
+        bulk_copy_g2s(reinterpret_cast<unsigned char*>(beta_z) + k * PG::BETA_PITCH,
+                      x.beta + first + k * (PG::BETA_CHUNK / sizeof(T)),
+                      (uint32_t)PG::BETA_CHUNK, &bars[1]);
+      if (usrc)
+        bulk_copy_g2s(reinterpret_cast<unsigned char*>(u_z) + k * PG::U_PITCH,
+                      usrc + first + k * (PG::U_CHUNK / sizeof(Q4<T>)), (uint32_t)PG::U_CHUNK,
+                      &bars[1]);
+    }
   };
 
   if (tid == 0) {
@@ -314,8 +337,32 @@ __global__ void __launch_bounds__(1024, 1)
       // load turns it into a failure of the whole CTA before anything is used
       bool ok = mbar_wait_bounded(&bars[0], par, kWaitNs);
       if (ok && a.u_load) ok = mbar_wait_bounded(&bars[1], par, kWaitNs);
-      const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_z + lrow) + c;
-      {
+      if constexpr (PG::SWAP) {
+        // Both components of every point (a 16-byte read, shared by the pair); thread c
+        // parks the full points m = 4c .. 4c + 3 of its 8, which it finishes in the epilogue.
+        float park[2 * E];
+#pragma unroll
+        for (int mm = 0; mm < E / 2; ++mm) {
+          Q4<T> pp[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int m = mm + h * (E / 2);
+            const int i = j + m * J;
+            Q4<T> p = psi_z[i];
+            if (a.u_load) p = apply_u(u_z[PG::upos(i)], p);
+            pp[h] = p;
+            if (a.sigma == 0) v[m] = {p.x + sg * p.z, p.y + sg * p.w};
+            else v[m] = {p.x + sg * p.w, p.y - sg * p.z};
+          }
+          const Q4<T> mine = c ? pp[1] : pp[0];
+          park[4 * mm] = mine.x;
+          park[4 * mm + 1] = mine.y;
+          park[4 * mm + 2] = mine.z;
+          park[4 * mm + 3] = mine.w;
+        }
+        tmem_st16(tpark, park);
+      } else {
+        const Cx<T>* src_c = reinterpret_cast<const Cx<T>*>(psi_z + lrow) + c;
         float park[2 * E];
 #pragma unroll
         for (int m = 0; m < E; ++m) {
@@ -388,26 +435,51 @@ __global__ void __launch_bounds__(1024, 1)
         done[1] += 1;
         tmem_wait_st();
         Q4<T>* stage = reinterpret_cast<Q4<T>*>(psmem);
-        Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
+        if constexpr (PG::SWAP) {
+          // eigencomponent results of the pair meet in the staging buffer (the partner is
+          // the neighbouring lane); thread c then finishes points m = 4c .. 4c + 3
+          Cx<T>* stc = reinterpret_cast<Cx<T>*>(stage) + c;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float pk[E];
-          tmem_ld8(tpark + (uint32_t)(h * E), pk);
+          for (int m = 0; m < E; ++m) stc[2 * PG::spos(j + m * J)] = v[m];
+          __syncwarp();
+          float pk[2 * E];
+          tmem_ld16(tpark, pk);
           tmem_wait_ld_regs(pk);
 #pragma unroll
           for (int mm = 0; mm < E / 2; ++mm) {
-            const int m = h * (E / 2) + mm;
-            const int i = j + m * J;
-            const Cx<T> oth = shfl_pair(v[m]);
-            const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
-            Cx<T> d;
-            if (c == 0) d = cadd(dp, dm);
-            else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
-            const Cx<T> p = {pk[2 * mm], pk[2 * mm + 1]};
-            const T bm1 = a.beta ? beta_z[lrow + i] : T(0);
-            Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
-            if (a.u_store) o = apply_u_row(u_z[lrow + i], o, shfl_pair(o), c);
-            my_stage[2 * i] = o;
+            const int i = j + (4 * c + mm) * J;
+            const Q4<T> dd = stage[PG::spos(i)];  // (D+, D-)
+            const Cx<T> dp = {dd.x, dd.y}, dm = {dd.z, dd.w};
+            const Cx<T> d1 = cadd(dp, dm);
+            const Cx<T> d2 = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+            const T bm1 = a.beta ? beta_z[PG::bpos(i)] : T(0);
+            Q4<T> o = {(pk[4 * mm] + d1.re) + bm1 * d1.re, (pk[4 * mm + 1] + d1.im) + bm1 * d1.im,
+                       (pk[4 * mm + 2] + d2.re) + bm1 * d2.re, (pk[4 * mm + 3] + d2.im) + bm1 * d2.im};
+            if (a.u_store) o = apply_u(u_z[PG::upos(i)], o);
+            stage[PG::spos(i)] = o;
+          }
+        } else {
+          Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float pk[E];
+            tmem_ld8(tpark + (uint32_t)(h * E), pk);
+            tmem_wait_ld_regs(pk);
+#pragma unroll
+            for (int mm = 0; mm < E / 2; ++mm) {
+              const int m = h * (E / 2) + mm;
+              const int i = j + m * J;
+              const Cx<T> oth = shfl_pair(v[m]);
+              const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
+              Cx<T> d;
+              if (c == 0) d = cadd(dp, dm);
+              else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+              const Cx<T> p = {pk[2 * mm], pk[2 * mm + 1]};
+              const T bm1 = a.beta ? beta_z[lrow + i] : T(0);
+              Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+              if (a.u_store) o = apply_u_row(u_z[lrow + i], o, shfl_pair(o), c);
+              my_stage[2 * i] = o;
+            }
           }
         }
       }
@@ -433,8 +505,8 @@ __global__ void __launch_bounds__(1024, 1)
         for (int q = 0; q < NIT; ++q) {
           const int itm = tid + q * PG::THREADS;
           const int gg = itm % GL, owner = gg / LPI;
-          const uint32_t off =
-              (uint32_t)(((gg - owner * LPI) * (L + 1) + i0 + itm / GL) * sizeof(Q4<T>));
+          const uint32_t off = (uint32_t)(((gg - owner * LPI) * (L + 1) + PG::spos(i0 + itm / GL)) *
+                                          sizeof(Q4<T>));
           val[q] = ld_dsmem_q4<T>(mapa_shared(local, owner) + off);
         }
       } else {
