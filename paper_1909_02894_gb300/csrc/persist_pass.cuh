@@ -401,7 +401,8 @@ __global__ void __launch_bounds__(1024, 1)
         fft_passes<T, L, E, false>(v, buf, j, a.tw);
 #pragma unroll
       for (int m = 0; m < E; ++m) {
-        if ((m & 3) == 0) asm volatile("" ::: "memory");
+        if constexpr (!PG::SWAP)
+          if ((m & 3) == 0) asm volatile("" ::: "memory");  // at most 4 loads in flight
         const Q4<T> q = ldg_q4(a.mult + j + m * J);
         const T vr = v[m].re, vi = v[m].im;
         const T sh = -sg * q.z, sl = -sg * q.w;
