@@ -65,9 +65,14 @@ def lib():
         L.oracle_observables.argtypes = [P, dp, dp, dp, dp, dp, dp]
         L.oracle_modes_evolve.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.c_long, C.c_int, dp, dp, dp, C.c_int, dp, dp, dp]
+        L.oracle_run_scheme.argtypes = [P, dp, dp, dp, C.c_double, C.c_long, C.c_int, dp]
+        L.oracle_modes_evolve_scheme.argtypes = [P, C.c_double, C.c_double, C.c_double,
+                                                 C.c_double, C.c_long, C.c_int, C.c_int, dp,
+                                                 dp, dp, C.c_int, dp, dp, dp]
         L.oracle_threads.argtypes = []
         for f in ("oracle_fft", "oracle_deriv", "oracle_coefficients", "oracle_half_step",
-                  "oracle_run", "oracle_observables", "oracle_modes_evolve", "oracle_threads"):
+                  "oracle_run", "oracle_observables", "oracle_modes_evolve", "oracle_threads",
+                  "oracle_run_scheme", "oracle_modes_evolve_scheme"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -162,13 +167,17 @@ def half_step(prob: Problem, dt):
     return u.reshape(prob.ny, prob.nx, 2, 2)
 
 
-def run(prob: Problem, psi, dt, n_steps):
+SCHEME_II, SCHEME_II_SYMMETRIC = 0, 1
+
+
+def run(prob: Problem, psi, dt, n_steps, scheme=SCHEME_II):
+    """n_steps of Scheme II (Sec. 5.2) or of its symmetric sub-step order."""
     psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
     assert psi.shape == (2, prob.ny, prob.nx)
     g = prob._g()
     p = prob._params()
-    _check(lib().oracle_run(C.byref(p), *[_ptr(x) for x in g], dt, int(n_steps), _ptr(psi)),
-           "run")
+    _check(lib().oracle_run_scheme(C.byref(p), *[_ptr(x) for x in g], dt, int(n_steps),
+                                   int(scheme), _ptr(psi)), "run")
     return psi
 
 
@@ -186,7 +195,7 @@ def observables(prob: Problem, psi, with_density=False):
     return res
 
 
-def modes_evolve(prob: Problem, g00, g11, g22, dt, n_steps, modes, ix, iy):
+def modes_evolve(prob: Problem, g00, g11, g22, dt, n_steps, modes, ix, iy, scheme=SCHEME_II):
     """modes = [(qx, qy, (A1, A2))]; returns [len(ix)][2] complex."""
     qx = np.array([m[0] for m in modes], dtype=np.int32)
     qy = np.array([m[1] for m in modes], dtype=np.int32)
@@ -195,9 +204,10 @@ def modes_evolve(prob: Problem, g00, g11, g22, dt, n_steps, modes, ix, iy):
     iy = np.ascontiguousarray(iy, dtype=np.int32)
     out = np.empty((ix.size, 2), dtype=np.complex128)
     p = prob._params()
-    _check(lib().oracle_modes_evolve(C.byref(p), g00, g11, g22, dt, int(n_steps), len(modes),
-                                     _ptr(qx), _ptr(qy), _ptr(amps), ix.size, _ptr(ix),
-                                     _ptr(iy), _ptr(out)), "modes_evolve")
+    _check(lib().oracle_modes_evolve_scheme(C.byref(p), g00, g11, g22, dt, int(n_steps),
+                                            int(scheme), len(modes), _ptr(qx), _ptr(qy),
+                                            _ptr(amps), ix.size, _ptr(ix), _ptr(iy),
+                                            _ptr(out)), "modes_evolve")
     return out
 
 

@@ -352,7 +352,13 @@ static void directional_substep(const oracle_params *p, int axis, double dt,
 
 int oracle_run(const oracle_params *p, const double *g00, const double *g11,
                const double *g22, double dt, long n_steps, cplx *psi) {
+  return oracle_run_scheme(p, g00, g11, g22, dt, n_steps, ORACLE_SCHEME_II, psi);
+}
+
+int oracle_run_scheme(const oracle_params *p, const double *g00, const double *g11,
+                      const double *g22, double dt, long n_steps, int scheme, cplx *psi) {
   if (check_params(p) || !psi || n_steps < 0 || !(dt > 0.0)) return -1;
+  if (scheme != ORACLE_SCHEME_II && scheme != ORACLE_SCHEME_II_SYMMETRIC) return -1;
   const size_t np = (size_t)p->nx * p->ny;
   cplx *u = malloc(sizeof(cplx) * 4 * np);
   cplx *b1 = malloc(sizeof(cplx) * np), *b2 = malloc(sizeof(cplx) * np);
@@ -361,10 +367,16 @@ int oracle_run(const oracle_params *p, const double *g00, const double *g11,
     rc = oracle_coefficients(p, g00, g11, g22, NULL, NULL, NULL, NULL, NULL, NULL, b1, b2);
   if (rc == 0) {
     for (long s = 0; s < n_steps; s++) {
-      apply_U(p, u, psi);                      /* S1 */
-      directional_substep(p, 0, dt, b1, psi);  /* S2 */
-      directional_substep(p, 1, dt, b2, psi);  /* S3 */
-      apply_U(p, u, psi);                      /* S4 */
+      apply_U(p, u, psi);                              /* S1 */
+      if (scheme == ORACLE_SCHEME_II) {
+        directional_substep(p, 0, dt, b1, psi);        /* S2 */
+        directional_substep(p, 1, dt, b2, psi);        /* S3 */
+      } else {
+        directional_substep(p, 0, 0.5 * dt, b1, psi);  /* x over dt/2 */
+        directional_substep(p, 1, dt, b2, psi);        /* y over dt   */
+        directional_substep(p, 0, 0.5 * dt, b1, psi);  /* x over dt/2 */
+      }
+      apply_U(p, u, psi);                              /* S4 */
     }
   }
   free(u); free(b1); free(b2);
@@ -445,7 +457,16 @@ int oracle_modes_evolve(const oracle_params *p, double g00, double g11, double g
                         double dt, long n_steps, int n_modes, const int *qx,
                         const int *qy, const cplx *amps, int n_pts, const int *ix,
                         const int *iy, cplx *out) {
+  return oracle_modes_evolve_scheme(p, g00, g11, g22, dt, n_steps, ORACLE_SCHEME_II, n_modes,
+                                    qx, qy, amps, n_pts, ix, iy, out);
+}
+
+int oracle_modes_evolve_scheme(const oracle_params *p, double g00, double g11, double g22,
+                               double dt, long n_steps, int scheme, int n_modes,
+                               const int *qx, const int *qy, const cplx *amps, int n_pts,
+                               const int *ix, const int *iy, cplx *out) {
   if (check_params(p) || p->pml_wx || p->pml_wy) return -1;
+  if (scheme != ORACLE_SCHEME_II && scheme != ORACLE_SCHEME_II_SYMMETRIC) return -1;
   if (!(g00 > 0.0 && g11 > 0.0 && g22 > 0.0) || n_steps < 0) return -1;
   const double a1 = p->c * sqrt(g00 / g11), a2 = p->c * sqrt(g00 / g22);
   const double me = p->mass * p->c * p->c * sqrt(g00);
@@ -454,7 +475,9 @@ int oracle_modes_evolve(const oracle_params *p, double g00, double g11, double g
   for (int s = 0; s < n_pts; s++) out[2 * s] = out[2 * s + 1] = 0.0;
   for (int m = 0; m < n_modes; m++) {
     if (qx[m] < 0 || qx[m] >= p->nx || qy[m] < 0 || qy[m] >= p->ny) return -1;
-    double tx = dt * xi_of(qx[m], p->nx, p->ax), ty = dt * xi_of(qy[m], p->ny, p->ay);
+    /* the x sub-step runs over dt (Scheme II) or twice over dt/2 around y (symmetric) */
+    const double hx_dt = scheme == ORACLE_SCHEME_II ? dt : 0.5 * dt;
+    double tx = hx_dt * xi_of(qx[m], p->nx, p->ax), ty = dt * xi_of(qy[m], p->ny, p->ay);
     cplx Kx[4] = {a1 * cos(tx) + (1.0 - a1), -I * a1 * sin(tx), -I * a1 * sin(tx),
                   a1 * cos(tx) + (1.0 - a1)};
     cplx Ky[4] = {a2 * cos(ty) + (1.0 - a2), -a2 * sin(ty), a2 * sin(ty),
@@ -462,6 +485,10 @@ int oracle_modes_evolve(const oracle_params *p, double g00, double g11, double g
     cplx T[4], tmp[4];
     mat2_mul(Kx, U, tmp);
     mat2_mul(Ky, tmp, T);
+    if (scheme == ORACLE_SCHEME_II_SYMMETRIC) {
+      mat2_mul(Kx, T, tmp);
+      memcpy(T, tmp, sizeof(T));
+    }
     mat2_mul(U, T, T);
     cplx v0 = amps[2 * m], v1 = amps[2 * m + 1];
     for (long s = 0; s < n_steps; s++) {

@@ -57,9 +57,18 @@ int oracle_coefficients(const oracle_params *p, const double *g00, const double 
 int oracle_half_step(const oracle_params *p, const double *g00, const double *g11,
                      const double *g22, double dt, double complex *u);
 
+enum { ORACLE_SCHEME_II = 0, ORACLE_SCHEME_II_SYMMETRIC = 1 };
+
 /* n_steps of Scheme II from psi (in place): U, x-substep, y-substep, U per step. */
 int oracle_run(const oracle_params *p, const double *g00, const double *g11,
                const double *g22, double dt, long n_steps, double complex *psi);
+
+/* The same with a choice of sub-step order: ORACLE_SCHEME_II as printed (Sec. 5.2), or
+ * its symmetric (Strang) ordering U, x-substep over dt/2, y-substep over dt, x-substep
+ * over dt/2, U per step, which the paper leaves to a remark on higher order (Sec. 5.3). */
+int oracle_run_scheme(const oracle_params *p, const double *g00, const double *g11,
+                      const double *g22, double dt, long n_steps, int scheme,
+                      double complex *psi);
 
 /* obs = {norm, norm_gamma, energy_re, energy_im}; density may be NULL. */
 int oracle_observables(const oracle_params *p, const double *g00, const double *g11,
@@ -74,6 +83,11 @@ int oracle_modes_evolve(const oracle_params *p, double g00, double g11, double g
                         double dt, long n_steps, int n_modes, const int *qx,
                         const int *qy, const double complex *amps, int n_pts,
                         const int *ix, const int *iy, double complex *out);
+/* The same for either sub-step order (ORACLE_SCHEME_*). */
+int oracle_modes_evolve_scheme(const oracle_params *p, double g00, double g11, double g22,
+                               double dt, long n_steps, int scheme, int n_modes,
+                               const int *qx, const int *qy, const double complex *amps,
+                               int n_pts, const int *ix, const int *iy, double complex *out);
 
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 int oracle_threads(void);

@@ -176,11 +176,15 @@ def test_t3_paper_2d_connection_is_quarter_d_ln_g00(oracle_lib):
 
 
 # --------------------------------------------------------------------------- T4
-def mode_step_matrix(a1, a2, me, dt, kx, ky):
-    """One step of the scheme on a plane wave, built from scipy's expm."""
+def mode_step_matrix(a1, a2, me, dt, kx, ky, symmetric=False):
+    """One step of the scheme on a plane wave, built from scipy's expm; symmetric: the
+    x sub-step twice over dt/2 around the y sub-step."""
     U = sla.expm(-1j * dt / 2 * me * SZ)
-    Kx = a1 * sla.expm(-1j * dt * kx * SX) + (1 - a1) * I2
     Ky = a2 * sla.expm(-1j * dt * ky * SY) + (1 - a2) * I2
+    if symmetric:
+        Kh = a1 * sla.expm(-1j * (dt / 2) * kx * SX) + (1 - a1) * I2
+        return U @ Kh @ Ky @ Kh @ U
+    Kx = a1 * sla.expm(-1j * dt * kx * SX) + (1 - a1) * I2
     return U @ Ky @ Kx @ U
 
 
@@ -351,7 +355,7 @@ def test_t8_spectral_convergence_in_h(oracle_lib):
 
 
 # --------------------------------------------------------------------------- T9
-def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
+def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt, symmetric=False):
     """The whole step as a dense 2N x 2N matrix from explicit DFT matrices, the spin
     connection from numpy's FFT derivative and U from scipy's expm."""
     npt = nx * ny
@@ -371,7 +375,7 @@ def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
                 for s in range(2):
                     Ub[r * npt + k, s * npt + k] = u[r, s]
 
-    def line_op(n, a, sig):
+    def line_op(n, a, sig, dt=dt):
         kk = np.arange(n)
         Fm = np.exp(-2j * np.pi * np.outer(kk, kk) / n)
         Fi = np.conj(Fm) / n
@@ -383,7 +387,7 @@ def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
                 blocks[r][s] = Fi @ np.diag(d) @ Fm
         return blocks
 
-    Bx = line_op(nx, ax, SX)
+    Bx = line_op(nx, ax, SX, dt / 2 if symmetric else dt)
     By = line_op(ny, ay, SY)
     Ix, Iy = np.eye(nx), np.eye(ny)
     Kx = np.zeros((2 * npt, 2 * npt), dtype=complex)
@@ -397,6 +401,8 @@ def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
     Id = np.eye(2 * npt)
     Sx = np.diag(b1) @ Kx + np.diag(1 - b1) @ Id
     Sy = np.diag(b2) @ Ky + np.diag(1 - b2) @ Id
+    if symmetric:
+        return Ub @ Sx @ Sy @ Sx @ Ub
     return Ub @ Sy @ Sx @ Ub
 
 
@@ -461,3 +467,95 @@ def test_pml_types_absorb(oracle_lib, ptype):
     n0 = oracle_lib.observables(pn, oracle_lib.run(pn, psi0, 0.05, 80))["norm"]
     n1 = oracle_lib.observables(pp, oracle_lib.run(pp, psi0, 0.05, 80))["norm"]
     assert n1 < 0.9 * n0
+
+
+# ------------------------------------------------------ symmetric sub-step order
+# The symmetric (Strang) ordering U, x over dt/2, y over dt, x over dt/2, U of Scheme II
+# (the second-order direction of Sec. 5.3's remark on higher order), pinned the same way
+# as the printed order: per-mode closed form, free propagator, dense brute force.
+@pytest.mark.parametrize("g,mass,c", [((1.0, 1.0, 1.0), 0.0, 1.0), ((1.3, 0.8, 1.1), 0.7, 1.2)])
+def test_symmetric_constant_metric_per_mode_closed_form(oracle_lib, g, mass, c):
+    nx, ny, ax, ay = 32, 16, 6.0, 4.0
+    modes = [(1, 0, (1.0, 0.5j)), (3, 14, (0.3 - 0.2j, 0.1)), (31, 5, (0.05, -0.4j)),
+             (16, 8, (0.02, 0.01))]
+    psi0 = W.plane_waves(nx, ny, ax, ay, modes)
+    G = [np.full((ny, nx), v) for v in g]
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=G[0], g11=G[1], g22=G[2])
+    dt, n = 0.03, 200
+    got = oracle_lib.run(prob, psi0, dt, n, scheme=oracle_lib.SCHEME_II_SYMMETRIC)
+    a1, a2 = c * np.sqrt(g[0] / g[1]), c * np.sqrt(g[0] / g[2])
+    me = mass * c * c * np.sqrt(g[0])
+    xs, ys = xi_vec(nx, ax), xi_vec(ny, ay)
+    X, Y = W.mesh(nx, ny, ax, ay)
+    ref = np.zeros_like(psi0)
+    for qx, qy, amps in modes:
+        T = mode_step_matrix(a1, a2, me, dt, xs[qx], ys[qy], symmetric=True)
+        v = np.linalg.matrix_power(T, n) @ np.array(amps)
+        e = np.exp(1j * xs[qx] * (X + ax) + 1j * ys[qy] * (Y + ay))
+        ref[0] += v[0] * e
+        ref[1] += v[1] * e
+    assert W.rel_l2(got, ref) <= 1e-12
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    pts = oracle_lib.modes_evolve(prob, *g, dt, n, modes, ii.ravel(), jj.ravel(),
+                                  scheme=oracle_lib.SCHEME_II_SYMMETRIC)
+    assert np.abs(pts[:, 0] - ref[0].ravel()).max() <= 1e-12
+    assert np.abs(pts[:, 1] - ref[1].ravel()).max() <= 1e-12
+
+
+def test_symmetric_second_order_convergence_to_free_propagator(oracle_lib):
+    """Flat space, exact solution exp(-i T H(xi)) per mode: the symmetric order has error
+    O(dt^2) (the printed order: O(dt), test T5)."""
+    n, a, mass, T = 64, 10.0, 0.5, 1.0
+    psi0 = W.wave_packet(n, n, a, a, 1.5, (1.0, -0.5))
+    psi0[1] = 0.5j * psi0[0]
+    prob = problem(oracle_lib, n, n, a, a, mass=mass)
+    xs = xi_vec(n, a)
+    KX, KY = np.meshgrid(xs, xs, indexing="xy")
+    E = np.sqrt(KX ** 2 + KY ** 2 + mass ** 2)
+    h0 = np.fft.fft2(psi0[0])
+    h1 = np.fft.fft2(psi0[1])
+    cs, sn = np.cos(T * E), np.sin(T * E) / E
+    r0 = cs * h0 - 1j * sn * (mass * h0 + (KX - 1j * KY) * h1)
+    r1 = cs * h1 - 1j * sn * ((KX + 1j * KY) * h0 - mass * h1)
+    exact = np.stack([np.fft.ifft2(r0), np.fft.ifft2(r1)])
+    errs = []
+    for dt in (0.04, 0.02, 0.01, 0.005):
+        got = oracle_lib.run(prob, psi0, dt, int(round(T / dt)),
+                             scheme=oracle_lib.SCHEME_II_SYMMETRIC)
+        errs.append(W.rel_l2(got, exact))
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(abs(o - 2.0) <= 0.15 for o in orders), (errs, orders)
+    assert errs[-1] < 1e-3
+
+
+def test_symmetric_brute_force_dense_step(oracle_lib):
+    nx, ny, ax, ay = 8, 4, 3.0, 2.0
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g00 = 1.0 + 0.2 * np.exp(-(X ** 2 + Y ** 2))
+    g11 = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + Y ** 2))
+    g22 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y - 0.3) ** 2))
+    mass, c, dt = 0.7, 1.1, 0.13
+    M = dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt, symmetric=True)
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=g00, g11=g11, g22=g22)
+    npt = nx * ny
+    for e in range(2 * npt):
+        v = np.zeros(2 * npt, dtype=complex)
+        v[e] = 1.0
+        got = oracle_lib.run(prob, v.reshape(2, ny, nx), dt, 1,
+                             scheme=oracle_lib.SCHEME_II_SYMMETRIC).ravel()
+        assert np.abs(got - M[:, e]).max() <= 1e-13
+
+
+def test_symmetric_equals_printed_order_on_y_independent_flat_states(oracle_lib):
+    """Flat space, psi constant along y: the y sub-step is the identity and the two x
+    half-steps compose to one x step, so both orders give the same result."""
+    nx, ny, a = 32, 8, 5.0
+    x = W.grid_1d(nx, a)
+    line = np.exp(-x ** 2 / 2 + 1.3j * x)
+    psi0 = np.zeros((2, ny, nx), complex)
+    psi0[0] = line[None, :]
+    psi0[1] = 0.3j * line[None, :]
+    prob = problem(oracle_lib, nx, ny, a, a, mass=0.6)
+    a_ = oracle_lib.run(prob, psi0, 0.05, 40)
+    b_ = oracle_lib.run(prob, psi0, 0.05, 40, scheme=oracle_lib.SCHEME_II_SYMMETRIC)
+    assert W.rel_l2(b_, a_) <= 1e-13
