@@ -55,6 +55,13 @@ typedef enum {
 
 typedef enum { DIRAC_C64 = 0, DIRAC_C128 = 1 } dirac_precision;
 
+/* Order of the sub-steps within one time step (Sec. 5.2, Scheme II): SCHEME_II is the
+ * printed order U, x, y, U (first order in time, Prop. 5.2); SCHEME_II_SYMMETRIC runs the
+ * x sub-step twice over dt/2 around the y sub-step (U, x/2, y, x/2, U), the symmetric
+ * splitting the paper's remark on higher order in time (Sec. 5.3) points to; second
+ * order in time in flat space. The symmetric order costs three line passes per step. */
+typedef enum { DIRAC_SCHEME_II = 0, DIRAC_SCHEME_II_SYMMETRIC = 1 } dirac_scheme;
+
 /* Spin connection Omega_j (Sec. 2.2). COVARIANT: Omega_j = 1/2 d_j ln(w a^j) with
  * w = sqrt(g11 g22 / g00) (= sqrt|g| g^00, the weight of the conserved norm, eq. l2gamma).
  * PAPER_2D: Omega_j = 1/2 d_j Phi with g00 = exp(2 Phi), as printed for Experiment 3.
@@ -136,6 +143,13 @@ const char *dirac_last_error(const dirac_ctx *ctx);
 
 /* Releases the context and all its device memory. NULL is allowed. */
 void dirac_destroy(dirac_ctx *ctx);
+
+/* Selects the sub-step order of later dirac_step calls (dirac_scheme; the default is
+ * DIRAC_SCHEME_II). The symmetric order needs two more device arrays (x-pass multipliers
+ * for dt/2 and U^2 in the normal layout), allocated on the next dirac_step. Contexts
+ * with the symmetric order cannot join a batch (dirac_batch_submit returns
+ * DIRAC_EUNSUPPORTED). DIRAC_EINVAL for other values. */
+dirac_status dirac_set_scheme(dirac_ctx *ctx, int scheme);
 
 /* CTA shape of the two fused passes (each pass: FFT along a line, k-space multiply,
  * inverse FFT, combine, transposed store): about 256 or 512 threads per CTA for that

@@ -22,13 +22,14 @@ STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_EINVAL", 2: "DIRAC_ENOMEM", 3: "DIRAC_E
                 4: "DIRAC_ECUDA", 5: "DIRAC_ETIMEOUT", 6: "DIRAC_ENONFINITE", 7: "DIRAC_ESTATE"}
 DIRAC_C64, DIRAC_C128 = 0, 1
 DIRAC_CONN_COVARIANT, DIRAC_CONN_PAPER_2D, DIRAC_CONN_NONE = 0, 1, 2
+DIRAC_SCHEME_II, DIRAC_SCHEME_II_SYMMETRIC = 0, 1
 
 # Every symbol the header declares; the CPU tests check that the library exports them.
 ABI_SYMBOLS = (
     "dirac_create", "dirac_set_state", "dirac_get_state", "dirac_step",
     "dirac_observables", "dirac_synchronize", "dirac_last_error", "dirac_destroy",
     "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc", "dirac_footprint_bytes",
-    "dirac_autotune", "dirac_test_timeout_next_step",
+    "dirac_autotune", "dirac_test_timeout_next_step", "dirac_set_scheme",
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
@@ -95,6 +96,7 @@ def lib():
         L.dirac_destroy.argtypes = [vp]
         L.dirac_destroy.restype = None
         L.dirac_set_launch.argtypes = [vp, i, i]
+        L.dirac_set_scheme.argtypes = [vp, i]
         L.dirac_launch_count.argtypes = [vp]
         L.dirac_launch_count.restype = l
         L.dirac_norms_noalloc.argtypes = [vp, vp, i, i, d, d, vp, vp]
@@ -216,6 +218,10 @@ def dirac_set_launch(ctx, threads_x: int, threads_y: int):
     _check(lib().dirac_set_launch(ctx, int(threads_x), int(threads_y)), ctx)
 
 
+def dirac_set_scheme(ctx, scheme: int):
+    _check(lib().dirac_set_scheme(ctx, int(scheme)), ctx)
+
+
 def dirac_launch_count(ctx) -> int:
     return int(lib().dirac_launch_count(ctx))
 
@@ -315,7 +321,8 @@ def dirac_destroy(ctx):
 class Simulation:
     """Owns one context; marshalling only (same calls as the C ABI)."""
 
-    def __init__(self, workload, precision=DIRAC_C64, stream=None, conn=None):
+    def __init__(self, workload, precision=DIRAC_C64, stream=None, conn=None,
+                 scheme=DIRAC_SCHEME_II):
         w = workload
         self.nx, self.ny = w.nx, w.ny
         self.ctx = dirac_create(
@@ -323,6 +330,8 @@ class Simulation:
             conn=w.conn if conn is None else conn, mass=w.mass, c=w.c,
             pml_wx=w.pml_width_x, pml_wy=w.pml_width_y, pml_type=w.pml_type,
             sigma0=w.sigma0, theta=w.theta, precision=precision, stream=stream)
+        if scheme != DIRAC_SCHEME_II:
+            dirac_set_scheme(self.ctx, scheme)
 
     def set_state(self, psi):
         dirac_set_state(self.ctx, psi)

@@ -335,6 +335,8 @@ dirac_status dirac_batch_submit(dirac_batch* b, dirac_ctx* inst, long n_steps, d
   *slot = -1;
   if (inst->prec != b->prec) return bfail(b, DIRAC_EINVAL, "precision differs from the batch");
   if (!inst->state_set) return bfail(b, DIRAC_ESTATE, "set_state must come before submit");
+  if (inst->scheme != DIRAC_SCHEME_II)
+    return bfail(b, DIRAC_EUNSUPPORTED, "the batch runs the printed sub-step order only");
   if (n_steps < 1) return bfail(b, DIRAC_EINVAL, "n_steps must be >= 1");
   if (!(dt > 0.0)) return bfail(b, DIRAC_EINVAL, "dt must be positive");
   for (const Slot& s : b->slots)

@@ -32,6 +32,9 @@ struct dirac_ctx {
   void *scratch1 = nullptr, *scratch2 = nullptr;
   double *partials = nullptr, *result = nullptr, *density = nullptr;
 
+  int scheme = DIRAC_SCHEME_II;
+  void *mult_xh = nullptr, *u2_n = nullptr;  // symmetric order: x multipliers at dt/2,
+                                             // U^2 in the normal layout
   int* d_err = nullptr;       // device error flag written by bounded waits
   double dt_cached = 0.0;
   bool state_set = false;

@@ -92,16 +92,72 @@ static LinePassArgs<T> pass_args(dirac_ctx* ctx, int axis) {
 template <typename T>
 static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
   cudaStream_t st = ctx->stream;
+  const bool sym = ctx->scheme == DIRAC_SCHEME_II_SYMMETRIC;
+  if (sym) {
+    if (!ctx->mult_xh) CK(dalloc(ctx, &ctx->mult_xh, ctx->nx * sizeof(Q4<T>)), "allocate tables");
+    if (!ctx->u_identity && !ctx->u2_n)
+      CK(dalloc(ctx, &ctx->u2_n, npts(ctx) * sizeof(Q4<T>)), "allocate half-step");
+  }
   if (!ctx->u_identity) {
     CK(launch_halfstep<T>(ctx->a1, ctx->a2, ctx->meff, ctx->omx, ctx->omy, ctx->nx, ctx->ny, dt,
-                          (Q4<T>*)ctx->u_n, (Q4<T>*)ctx->u_t, (Q4<T>*)ctx->u2_t, st),
+                          (Q4<T>*)ctx->u_n, (Q4<T>*)ctx->u_t, (Q4<T>*)ctx->u2_t,
+                          sym ? (Q4<T>*)ctx->u2_n : nullptr, st),
        "half-step matrices");
     ctx->launches += 1;
   }
   CK(launch_step_mult<T>(ctx->nx, ctx->ax, dt, (Q4<T>*)ctx->mult_x, st), "x multipliers");
   CK(launch_step_mult<T>(ctx->ny, ctx->ay, dt, (Q4<T>*)ctx->mult_y, st), "y multipliers");
   ctx->launches += 2;
+  if (sym) {
+    CK(launch_step_mult<T>(ctx->nx, ctx->ax, 0.5 * dt, (Q4<T>*)ctx->mult_xh, st),
+       "x multipliers (dt/2)");
+    ctx->launches += 1;
+  }
   ctx->dt_cached = dt;
+  return DIRAC_OK;
+}
+
+// Symmetric order: x over dt/2 (normal -> transposed), y over dt (transposed -> normal),
+// x over dt/2 (normal -> normal, into the other buffer); U on the first x pass's load,
+// U^2 / U on the last x pass's store. The state alternates between the two buffers and
+// ends in ctx->psi.
+template <typename T>
+static dirac_status step_symmetric(dirac_ctx* ctx, long n) {
+  LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
+  ax.mult = (const Q4<T>*)ctx->mult_xh;
+  ax.beta = (const T*)ctx->beta1;
+  ay.mult = (const Q4<T>*)ctx->mult_y;
+  ay.beta = (const T*)ctx->beta2T;
+  ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
+  ctx->test_timeout_next = 0;
+  void* cur = ctx->psi;
+  void* oth = ctx->psiT;
+  const int opt_x = pass_opt(ctx, ctx->threads_x, ctx->nx);
+  const int opt_y = pass_opt(ctx, ctx->threads_y, ctx->ny);
+  for (long s = 0; s < n; ++s) {
+    LinePassArgs<T> a1 = ax, a3 = ax;
+    a1.in = (const Q4<T>*)cur;
+    a1.out = (Q4<T>*)oth;
+    a1.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
+    ay.in = (const Q4<T>*)oth;
+    ay.out = (Q4<T>*)cur;
+    a3.in = (const Q4<T>*)cur;
+    a3.out = (Q4<T>*)oth;
+    a3.store_normal = 1;
+    a3.u_store = ctx->u_identity ? nullptr
+                                 : (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n);
+    CK(launch_line_pass<T>(a1, MODE_STEP, opt_x, ctx->stream), "x pass (dt/2)");
+    CK(launch_line_pass<T>(ay, MODE_STEP, opt_y, ctx->stream), "y pass");
+    CK(launch_line_pass<T>(a3, MODE_STEP, opt_x, ctx->stream), "x pass (dt/2, rows)");
+    ctx->launches += 3;
+    void* t = cur;
+    cur = oth;
+    oth = t;
+  }
+  if (cur != ctx->psi) {  // the two state buffers trade names
+    ctx->psiT = ctx->psi;
+    ctx->psi = cur;
+  }
   return DIRAC_OK;
 }
 
@@ -111,6 +167,7 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
     dirac_status s = tables_for_dt<T>(ctx, dt);
     if (s != DIRAC_OK) return s;
   }
+  if (ctx->scheme == DIRAC_SCHEME_II_SYMMETRIC) return step_symmetric<T>(ctx, n);
   LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
   ax.in = (const Q4<T>*)ctx->psi;
   ax.out = (Q4<T>*)ctx->psiT;
@@ -551,6 +608,17 @@ void dirac_destroy(dirac_ctx* ctx) {
   free_all(ctx);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
+}
+
+dirac_status dirac_set_scheme(dirac_ctx* ctx, int scheme) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (scheme != DIRAC_SCHEME_II && scheme != DIRAC_SCHEME_II_SYMMETRIC)
+    return fail(ctx, DIRAC_EINVAL, "scheme must be DIRAC_SCHEME_II or DIRAC_SCHEME_II_SYMMETRIC");
+  if (scheme != ctx->scheme) {
+    ctx->scheme = scheme;
+    ctx->dt_cached = 0.0;  // the tables of the new order are made on the next step
+  }
+  return DIRAC_OK;
 }
 
 dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_pass) {

@@ -42,12 +42,13 @@ template <typename T>
 cudaError_t launch_beta(const double* a1, const double* a2, const double* sxinv,
                         const double* syinv, int nx, int ny, T* beta1, T* beta2T,
                         cudaStream_t st);
-// Half-step matrices for dt: U (normal layout), U and U^2 (transposed layout), stored as
-// (c0 - 1, c1, c2, c3) in T.
+// Half-step matrices for dt: U (normal layout), U and U^2 (transposed layout) and, if
+// u2_n is not null, U^2 in the normal layout, stored as (c0 - 1, c1, c2, c3) in T.
 template <typename T>
 cudaError_t launch_halfstep(const double* a1, const double* a2, const double* meff,
                             const double* omx, const double* omy, int nx, int ny, double dt,
-                            Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, cudaStream_t st);
+                            Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, Q4<T>* u2_n,
+                            cudaStream_t st);
 // Per-axis tables: per-pass twiddle blocks (layout in line_pass.cuh); step multipliers
 // ((cos(dt xi) - 1)/n, sin(dt xi)/n) as hi/lo pairs; derivative multipliers xi/n.
 template <typename T>

@@ -65,6 +65,8 @@ struct LinePassArgs {
   int inst_capacity;        // batched launch: table entries (host side, sizes the grid)
   unsigned test_extra_tx;   // test hook: bytes a bulk copy never delivers (0 normally);
                             // makes the persistent pass's bounded wait run out
+  int store_normal;         // step mode: 0 = out is [L][n_lines] (transposed store),
+                            // 1 = out is [n_lines][L] like `in` (out must not alias in)
 };
 
 // Batched launches: a block (or group) of lines belongs to instance `k`; take that
@@ -499,7 +501,8 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       const T bm1 = a.beta ? a.beta[gi] : T(0);
       Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
       if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
-      my_stage[2 * i] = o;
+      if (a.store_normal) reinterpret_cast<Cx<T>*>(a.out)[2 * gi + c] = o;
+      else my_stage[2 * i] = o;
     } else {
       my_stage[2 * i] = v[m];
     }
@@ -519,6 +522,8 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
   const int line0 = (blk / CS) * GL;
   const int i0 = rank * ROWS;
   constexpr int HALF = Gm::NIT / 2;
+  // (a normal-layout store happened in the epilogue)
+  if (!(MODE == MODE_STEP && a.store_normal)) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     Q4<T> val[HALF];
@@ -541,6 +546,7 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       const int i = i0 + it / GL;
       a.out[(size_t)i * a.n_lines + line0 + g] = val[q];
     }
+  }
   }
   if constexpr (CS > 1) cg::this_cluster().sync();
 }

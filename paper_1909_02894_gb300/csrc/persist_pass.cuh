@@ -493,7 +493,17 @@ __global__ void __launch_bounds__(1024, 1)
       if (tid == 0) issue_bu((s + n_clusters) * CS + rank);
       issued[1] += 1;
     }
-    if (!failed) {
+    if (!failed && a.store_normal) {
+      // rows back in the input's layout: this CTA's own lines, contiguous
+      const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(psmem);
+      constexpr int NIT = LPI * L / PG::THREADS;
+#pragma unroll
+      for (int q = 0; q < NIT; ++q) {
+        const int idx = tid + q * PG::THREADS;
+        const int l = idx / L, i = idx - l * L;
+        a.out[gfirst + idx] = stage[(size_t)l * (L + 1) + PG::spos(i)];
+      }
+    } else if (!failed) {
       const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(psmem);
       const int line0 = (int)(gfirst / L) - rank * LPI;
       const int i0 = rank * (L / CS);

@@ -147,7 +147,7 @@ __device__ inline void pauli_exp(double v1, double v2, double hm, double* out) {
 template <typename T>
 __global__ void k_halfstep(const double* a1, const double* a2, const double* meff,
                            const double* omx, const double* omy, int nx, int ny, double dt,
-                           Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t) {
+                           Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, Q4<T>* u2_n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nx * ny) return;
   const int j = k / nx, i = k - j * nx;
@@ -163,14 +163,16 @@ __global__ void k_halfstep(const double* a1, const double* a2, const double* mef
   u_n[k] = U;
   u_t[(size_t)i * ny + j] = U;
   u2_t[(size_t)i * ny + j] = U2;
+  if (u2_n) u2_n[k] = U2;
 }
 
 template <typename T>
 cudaError_t launch_halfstep(const double* a1, const double* a2, const double* meff,
                             const double* omx, const double* omy, int nx, int ny, double dt,
-                            Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, cudaStream_t st) {
+                            Q4<T>* u_n, Q4<T>* u_t, Q4<T>* u2_t, Q4<T>* u2_n,
+                            cudaStream_t st) {
   k_halfstep<T><<<nblocks((size_t)nx * ny), TPB, 0, st>>>(a1, a2, meff, omx, omy, nx, ny, dt,
-                                                          u_n, u_t, u2_t);
+                                                          u_n, u_t, u2_t, u2_n);
   return cudaGetLastError();
 }
 
@@ -286,7 +288,7 @@ cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cu
                                       const double*, int, int, T*, T*, cudaStream_t);        \
   template cudaError_t launch_halfstep<T>(const double*, const double*, const double*,      \
                                           const double*, const double*, int, int, double,    \
-                                          Q4<T>*, Q4<T>*, Q4<T>*, cudaStream_t);             \
+                                          Q4<T>*, Q4<T>*, Q4<T>*, Q4<T>*, cudaStream_t);     \
   template cudaError_t launch_twiddles<T>(int, int, Cx<T>*, cudaStream_t);                    \
   template cudaError_t launch_step_mult<T>(int, double, double, Q4<T>*, cudaStream_t);        \
   template cudaError_t launch_deriv_mult<T>(int, double, Q4<T>*, cudaStream_t);               \
