@@ -199,16 +199,16 @@ def run_reference(args, wl_name):
     return 0
 
 
-def cpu_baseline(w):
+def cpu_baseline(w, scheme=0):
     """Oracle timing on a bounded sample of the same workload (about 10-30 s of CPU)."""
     import oracle
 
     oracle.build()
     prob = oracle.Problem.from_workload(w)
     t0 = time.perf_counter()
-    oracle.run(prob, w.psi0, w.dt, 1)
+    oracle.run(prob, w.psi0, w.dt, 1, scheme=scheme)
     t1 = time.perf_counter()
-    oracle.run(prob, w.psi0, w.dt, 2)
+    oracle.run(prob, w.psi0, w.dt, 2, scheme=scheme)
     t2 = time.perf_counter()
     per_step = max((t2 - t1) - (t1 - t0), 1e-9)
     return {"value": w.nx * w.ny / per_step, "unit": UNIT, "cores": oracle.threads(),
@@ -367,6 +367,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--sustainable-rate", type=float, default=4.0)
     ap.add_argument("--sustainable-seconds", type=float, default=20.0)
+    ap.add_argument("--scheme", default="printed", choices=["printed", "symmetric"],
+                    help="sub-step order: printed (x, y) or symmetric (x/2, y, x/2)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -387,10 +389,16 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     w, prec_name, bytes_pt = workload(args.workload)
     prec = D.DIRAC_C64 if prec_name == "c64" else D.DIRAC_C128
+    symmetric = args.scheme == "symmetric"
+    passes = 3 if symmetric else 2
+    if symmetric:
+        # three sweeps of psi, b - 1 read in each, U^2 once: 124 B (complex64)
+        bytes_pt = bytes_pt // 88 * 124
     # A dedicated stream: the default stream's handle is 0, which the ABI reads as
     # "create a private stream", and events must be recorded where the kernels run.
     stream = torch.cuda.Stream()
-    sim = D.Simulation(w, precision=prec, stream=stream.cuda_stream)
+    sim = D.Simulation(w, precision=prec, stream=stream.cuda_stream,
+                       scheme=D.DIRAC_SCHEME_II_SYMMETRIC if symmetric else D.DIRAC_SCHEME_II)
     sim.set_state(w.psi0)
     pts = w.nx * w.ny
     warm = max(3, args.warmup)
@@ -420,13 +428,14 @@ def main():
     ms = float(ms_t.item())
     value = pts * args.steps * world / (ms * 1e-3)
 
-    # ---- roofline of the dominant kernel (the fused line pass, 2 launches per step;
-    # the timed region holds nothing else, so its average launch duration is ms/launches)
+    # ---- roofline of the dominant kernel (the fused line pass, 2 launches per step, 3 in
+    # the symmetric order; the timed region holds nothing else, so its average launch
+    # duration is ms/launches)
     peak, peak_kind = hbm_peak()
     per_launch_s = ms * 1e-3 / max(1, launches)
-    alg_bytes_launch = bytes_pt * pts / 2.0
+    alg_bytes_launch = bytes_pt * pts / float(passes)
     achieved = alg_bytes_launch / per_launch_s / 1e9
-    traffic = ncu_traffic(args.workload)
+    traffic = None if symmetric else ncu_traffic(args.workload)
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -455,6 +464,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == D.DIRAC_C64 else "f64", "data": "synthetic",
             "config": {"workload": w.name, "precision": prec_name, "grid": [w.nx, w.ny],
+                       "scheme": "Scheme II, symmetric x/2-y-x/2" if symmetric
+                       else "Scheme II (x, y)",
                        "dt": w.dt, "absorber": w.pml_width_x, "parallelism": "replicas",
                        "l2": "inputs larger than L2 (no flush)"
                        if bytes_pt * pts > L2_BYTES else "working set fits L2"},
@@ -467,7 +478,7 @@ def main():
             "e2e": e2e,
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w)
+            line["cpu_baseline"] = cpu_baseline(w, scheme=1 if symmetric else 0)
         print(json.dumps(line))
     sim.close()
     if world > 1:
