@@ -57,9 +57,9 @@ typedef enum { DIRAC_C64 = 0, DIRAC_C128 = 1 } dirac_precision;
 
 /* Order of the sub-steps within one time step (Sec. 5.2, Scheme II): SCHEME_II is the
  * printed order U, x, y, U (first order in time, Prop. 5.2); SCHEME_II_SYMMETRIC runs the
- * x sub-step twice over dt/2 around the y sub-step (U, x/2, y, x/2, U), the symmetric
- * splitting the paper's remark on higher order in time (Sec. 5.3) points to; second
- * order in time in flat space. The symmetric order costs three line passes per step. */
+ * x sub-step twice over dt/2 around the y sub-step (U, x/2, y, x/2, U): the symmetric
+ * (Strang) decomposition the paper's time discretization uses in flat space (Sec. 3,
+ * eq. op_flat) carried over to the direction split; second order in time in flat space. The symmetric order costs three line passes per step. */
 typedef enum { DIRAC_SCHEME_II = 0, DIRAC_SCHEME_II_SYMMETRIC = 1 } dirac_scheme;
 
 /* Spin connection Omega_j (Sec. 2.2). COVARIANT: Omega_j = 1/2 d_j ln(w a^j) with

@@ -65,7 +65,8 @@ int oracle_run(const oracle_params *p, const double *g00, const double *g11,
 
 /* The same with a choice of sub-step order: ORACLE_SCHEME_II as printed (Sec. 5.2), or
  * its symmetric (Strang) ordering U, x-substep over dt/2, y-substep over dt, x-substep
- * over dt/2, U per step, which the paper leaves to a remark on higher order (Sec. 5.3). */
+ * over dt/2, U per step: the symmetric decomposition of Sec. 3 (eq. op_flat) applied to
+ * the direction split as well. */
 int oracle_run_scheme(const oracle_params *p, const double *g00, const double *g11,
                       const double *g22, double dt, long n_steps, int scheme,
                       double complex *psi);

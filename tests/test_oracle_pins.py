@@ -471,8 +471,9 @@ def test_pml_types_absorb(oracle_lib, ptype):
 
 # ------------------------------------------------------ symmetric sub-step order
 # The symmetric (Strang) ordering U, x over dt/2, y over dt, x over dt/2, U of Scheme II
-# (the second-order direction of Sec. 5.3's remark on higher order), pinned the same way
-# as the printed order: per-mode closed form, free propagator, dense brute force.
+# (Sec. 3's second-order symmetric decomposition, eq. op_flat, applied to the direction
+# split), pinned the same way as the printed order: per-mode closed form, free
+# propagator, dense brute force.
 @pytest.mark.parametrize("g,mass,c", [((1.0, 1.0, 1.0), 0.0, 1.0), ((1.3, 0.8, 1.1), 0.7, 1.2)])
 def test_symmetric_constant_metric_per_mode_closed_form(oracle_lib, g, mass, c):
     nx, ny, ax, ay = 32, 16, 6.0, 4.0
