@@ -66,13 +66,17 @@ def lib():
         L.oracle_modes_evolve.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_double,
                                           C.c_long, C.c_int, dp, dp, dp, C.c_int, dp, dp, dp]
         L.oracle_run_scheme.argtypes = [P, dp, dp, dp, C.c_double, C.c_long, C.c_int, dp]
+        L.oracle_apply_A.argtypes = [P, dp, dp, dp, dp, dp]
+        L.oracle_bessel_j.argtypes = [C.c_double, C.c_int, dp]
+        L.oracle_run_poly.argtypes = [P, dp, dp, dp, C.c_double, C.c_long, C.c_int, C.c_int, dp]
         L.oracle_modes_evolve_scheme.argtypes = [P, C.c_double, C.c_double, C.c_double,
                                                  C.c_double, C.c_long, C.c_int, C.c_int, dp,
                                                  dp, dp, C.c_int, dp, dp, dp]
         L.oracle_threads.argtypes = []
         for f in ("oracle_fft", "oracle_deriv", "oracle_coefficients", "oracle_half_step",
                   "oracle_run", "oracle_observables", "oracle_modes_evolve", "oracle_threads",
-                  "oracle_run_scheme", "oracle_modes_evolve_scheme"):
+                  "oracle_run_scheme", "oracle_modes_evolve_scheme", "oracle_apply_A",
+                  "oracle_bessel_j", "oracle_run_poly"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -178,6 +182,33 @@ def run(prob: Problem, psi, dt, n_steps, scheme=SCHEME_II):
     p = prob._params()
     _check(lib().oracle_run_scheme(C.byref(p), *[_ptr(x) for x in g], dt, int(n_steps),
                                    int(scheme), _ptr(psi)), "run")
+    return psi
+
+
+POLY_TAYLOR, POLY_CHEBYSHEV = 0, 1
+
+
+def apply_A(prob: Problem, psi):
+    """A psi = - sum_j b^j sigma_j [[d_j]] psi (the unsplit middle-step operator)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128)
+    out = np.empty_like(psi)
+    _check(lib().oracle_apply_A(C.byref(prob._params()), *[_ptr(x) for x in prob._g()],
+                                _ptr(psi), _ptr(out)), "apply_A")
+    return out
+
+
+def bessel_j(x, n):
+    out = np.empty(n + 1)
+    _check(lib().oracle_bessel_j(float(x), int(n), _ptr(out)), "bessel_j")
+    return out
+
+
+def run_poly(prob: Problem, psi, dt, n_steps, family=POLY_CHEBYSHEV, order=8):
+    """n_steps of the polynomial scheme (eq. poly) with a Taylor or Chebyshev middle step."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    _check(lib().oracle_run_poly(C.byref(prob._params()), *[_ptr(x) for x in prob._g()],
+                                 float(dt), int(n_steps), int(family), int(order), _ptr(psi)),
+           "run_poly")
     return psi
 
 

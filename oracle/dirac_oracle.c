@@ -384,6 +384,143 @@ int oracle_run_scheme(const oracle_params *p, const double *g00, const double *g
 }
 
 /* ---------------------------------------------------------------------------------
+ * Unsplit middle step (Sec. 4.2 eq. op_split_poly, Sec. 5 eq. poly). The operator is
+ * A psi = - sum_j b^j sigma_j [[d_j]] psi with sigma_x (u, v) = (v, u) and
+ * sigma_y (u, v) = (-i v, i u); d is scratch of 2 np points.
+ * ------------------------------------------------------------------------------- */
+static void apply_A(const oracle_params *p, const cplx *b1, const cplx *b2, const cplx *in,
+                    cplx *out, cplx *d) {
+  const size_t np = (size_t)p->nx * p->ny;
+  oracle_deriv(p, 0, in, d);
+  oracle_deriv(p, 0, in + np, d + np);
+  for (size_t k = 0; k < np; k++) {
+    out[k] = -b1[k] * d[np + k];
+    out[np + k] = -b1[k] * d[k];
+  }
+  oracle_deriv(p, 1, in, d);
+  oracle_deriv(p, 1, in + np, d + np);
+  for (size_t k = 0; k < np; k++) {
+    out[k] += -b2[k] * (-I * d[np + k]);
+    out[np + k] += -b2[k] * (I * d[k]);
+  }
+}
+
+int oracle_apply_A(const oracle_params *p, const double *g00, const double *g11,
+                   const double *g22, const cplx *in, cplx *out) {
+  if (check_params(p) || !in || !out || in == out) return -1;
+  const size_t np = (size_t)p->nx * p->ny;
+  cplx *b1 = malloc(sizeof(cplx) * np), *b2 = malloc(sizeof(cplx) * np);
+  cplx *d = malloc(sizeof(cplx) * 2 * np);
+  int rc = oracle_coefficients(p, g00, g11, g22, NULL, NULL, NULL, NULL, NULL, NULL, b1, b2);
+  if (rc == 0) apply_A(p, b1, b2, in, out, d);
+  free(b1); free(b2); free(d);
+  return rc;
+}
+
+/* J_0 .. J_n by Miller's backward recurrence J_{k-1} = (2k/x) J_k - J_{k+1}, started far
+ * above max(n, x) and normalised with J_0 + 2 sum_k J_2k = 1. */
+int oracle_bessel_j(double x, int n, double *j) {
+  if (!(x >= 0.0) || n < 0 || !j) return -1;
+  for (int k = 0; k <= n; k++) j[k] = 0.0;
+  if (x == 0.0) {
+    j[0] = 1.0;
+    return 0;
+  }
+  int m = (n > (int)x ? n : (int)x) + 40 + (int)sqrt(40.0 * (n + x));
+  m += m & 1;
+  double up = 0.0, cur = 1e-280, sum = 0.0;
+  for (int k = m; k >= 1; k--) {
+    const double low = (2.0 * k / x) * cur - up;  /* J_{k-1} up to a common factor */
+    up = cur;
+    cur = low;
+    if (fabs(cur) > 1e250) {  /* rescale everything kept so far */
+      cur *= 1e-250;
+      up *= 1e-250;
+      sum *= 1e-250;
+      for (int t = 0; t <= n; t++) j[t] *= 1e-250;
+    }
+    if (k - 1 <= n) j[k - 1] = cur;
+    if (k - 1 >= 2 && (k - 1) % 2 == 0) sum += 2.0 * cur;
+  }
+  sum += cur;  /* J_0 */
+  for (int k = 0; k <= n; k++) j[k] /= sum;
+  return 0;
+}
+
+static double poly_bound(const oracle_params *p, const cplx *b1, const cplx *b2, double dt) {
+  const size_t np = (size_t)p->nx * p->ny;
+  double m1 = 0.0, m2 = 0.0;
+  for (size_t k = 0; k < np; k++) {
+    if (cabs(b1[k]) > m1) m1 = cabs(b1[k]);
+    if (cabs(b2[k]) > m2) m2 = cabs(b2[k]);
+  }
+  const double hx = 2.0 * p->ax / p->nx, hy = 2.0 * p->ay / p->ny;
+  return dt * (m1 * PI / hx + m2 * PI / hy);
+}
+
+int oracle_run_poly(const oracle_params *p, const double *g00, const double *g11,
+                    const double *g22, double dt, long n_steps, int family, int order,
+                    cplx *psi) {
+  if (check_params(p) || !psi || n_steps < 0 || !(dt > 0.0)) return -1;
+  if ((family != ORACLE_POLY_TAYLOR && family != ORACLE_POLY_CHEBYSHEV) || order < 1 ||
+      order > 256)
+    return -1;
+  const size_t np = (size_t)p->nx * p->ny, n2 = 2 * np;
+  cplx *u = malloc(sizeof(cplx) * 4 * np);
+  cplx *b1 = malloc(sizeof(cplx) * np), *b2 = malloc(sizeof(cplx) * np);
+  cplx *t0 = malloc(sizeof(cplx) * n2), *t1 = malloc(sizeof(cplx) * n2);
+  cplx *t2 = malloc(sizeof(cplx) * n2), *acc = malloc(sizeof(cplx) * n2);
+  cplx *d = malloc(sizeof(cplx) * n2);
+  double *jq = malloc(sizeof(double) * (order + 1));
+  int rc = oracle_half_step(p, g00, g11, g22, dt, u);
+  if (rc == 0)
+    rc = oracle_coefficients(p, g00, g11, g22, NULL, NULL, NULL, NULL, NULL, NULL, b1, b2);
+  const double R = rc == 0 ? poly_bound(p, b1, b2, dt) : 0.0;
+  if (rc == 0 && family == ORACLE_POLY_CHEBYSHEV) rc = oracle_bessel_j(R, order, jq);
+  for (long s = 0; rc == 0 && s < n_steps; s++) {
+    apply_U(p, u, psi);
+    if (family == ORACLE_POLY_TAYLOR) {
+      /* acc = sum_q (dt A)^q / q! psi, term by term */
+      memcpy(acc, psi, sizeof(cplx) * n2);
+      memcpy(t0, psi, sizeof(cplx) * n2);
+      for (int q = 1; q <= order; q++) {
+        apply_A(p, b1, b2, t0, t1, d);
+        for (size_t k = 0; k < n2; k++) {
+          t0[k] = (dt / q) * t1[k];
+          acc[k] += t0[k];
+        }
+      }
+    } else {
+      /* phi_0 = psi, phi_1 = B psi, phi_{q+1} = 2 B phi_q - phi_{q-1}, B = (i dt / R) A;
+       * acc = sum_q c_q phi_q with c_q = (2 - delta_q0) (-i)^q J_q(R) */
+      cplx cq = 1.0;  /* (-i)^q */
+      memcpy(t0, psi, sizeof(cplx) * n2);
+      for (size_t k = 0; k < n2; k++) acc[k] = jq[0] * t0[k];
+      apply_A(p, b1, b2, t0, t1, d);
+      for (size_t k = 0; k < n2; k++) t1[k] *= I * dt / R;
+      cq *= -I;
+      for (size_t k = 0; k < n2; k++) acc[k] += 2.0 * cq * jq[1] * t1[k];
+      for (int q = 2; q <= order; q++) {
+        apply_A(p, b1, b2, t1, t2, d);
+        cq *= -I;
+        for (size_t k = 0; k < n2; k++) {
+          t2[k] = 2.0 * (I * dt / R) * t2[k] - t0[k];
+          acc[k] += 2.0 * cq * jq[q] * t2[k];
+        }
+        cplx *t = t0;
+        t0 = t1;
+        t1 = t2;
+        t2 = t;
+      }
+    }
+    memcpy(psi, acc, sizeof(cplx) * n2);
+    apply_U(p, u, psi);
+  }
+  free(u); free(b1); free(b2); free(t0); free(t1); free(t2); free(acc); free(d); free(jq);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------------------
  * Observables. norm = hx hy sum |psi|^2 (the discrete l2 norm of Prop. 5.3),
  * norm_gamma = hx hy sum w |psi|^2 (eq. l2gamma with the weight sqrt|g| g^00),
  * density = |psi_1|^2 + |psi_2|^2 (Sec. 6.2), and the energy

@@ -71,6 +71,26 @@ int oracle_run_scheme(const oracle_params *p, const double *g00, const double *g
                       const double *g22, double dt, long n_steps, int scheme,
                       double complex *psi);
 
+/* The unsplit middle-step operator of Sec. 4.2 (eqs. op_split_cn, op_split_poly) with
+ * alpha(x) = a(x).alpha (eq. alpha_form), the absorbing layer's a^j -> b^j = a^j/S^j
+ * (Sec. 3) and the spectral derivative (eq. trick):
+ *   A psi = - sum_j b^j sigma_j [[d_j]] psi      (in, out: [2][ny][nx]; may not alias). */
+int oracle_apply_A(const oracle_params *p, const double *g00, const double *g11,
+                   const double *g22, const double complex *in, double complex *out);
+
+/* Bessel functions J_0(x) .. J_n(x) (x >= 0), the Chebyshev coefficients of exp. */
+int oracle_bessel_j(double x, int n, double *j);
+
+enum { ORACLE_POLY_TAYLOR = 0, ORACLE_POLY_CHEBYSHEV = 1 };
+
+/* n_steps of the polynomial scheme (Sec. 5, eq. poly): U, then
+ * psi <- sum_q a_q P_q(dt A) psi (degree `order`), then U. TAYLOR: a_q P_q(z) = z^q / q!.
+ * CHEBYSHEV: with H = i dt A and a bound R >= |spectrum of H| (R = dt sum_j max|b^j| pi/h_j),
+ * exp(dt A) = exp(-i H) ~ sum_q (2 - delta_q0) (-i)^q J_q(R) T_q(H / R). */
+int oracle_run_poly(const oracle_params *p, const double *g00, const double *g11,
+                    const double *g22, double dt, long n_steps, int family, int order,
+                    double complex *psi);
+
 /* obs = {norm, norm_gamma, energy_re, energy_im}; density may be NULL. */
 int oracle_observables(const oracle_params *p, const double *g00, const double *g11,
                        const double *g22, const double complex *psi, double *obs,

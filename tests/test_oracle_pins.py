@@ -8,6 +8,7 @@ and invariants proved in the paper (Prop. 5.2, Prop. 5.3).
 import numpy as np
 import pytest
 import scipy.linalg as sla
+import scipy.special as sp_special
 
 from paper_1909_02894_gb300 import workloads as W
 
@@ -560,3 +561,112 @@ def test_symmetric_equals_printed_order_on_y_independent_flat_states(oracle_lib)
     a_ = oracle_lib.run(prob, psi0, 0.05, 40)
     b_ = oracle_lib.run(prob, psi0, 0.05, 40, scheme=oracle_lib.SCHEME_II_SYMMETRIC)
     assert W.rel_l2(b_, a_) <= 1e-13
+
+
+# ------------------------------------------------ unsplit middle step (eq. poly)
+def _poly_series(M, order, family, R=None):
+    """sum_q a_q P_q(M) of a 2x2 matrix M = dt A(xi) (Taylor), or the Chebyshev form
+    with H = i M, built from scipy's Bessel functions and numpy's Chebyshev recurrence."""
+    if family == "taylor":
+        out, term = np.eye(2, dtype=complex), np.eye(2, dtype=complex)
+        for q in range(1, order + 1):
+            term = term @ M / q
+            out = out + term
+        return out
+    H = 1j * M
+    Tm, Tq = np.eye(2, dtype=complex), H / R
+    out = sp_special.jv(0, R) * Tm + 2 * (-1j) * sp_special.jv(1, R) * Tq
+    for q in range(2, order + 1):
+        Tm, Tq = Tq, 2 * (H / R) @ Tq - Tm
+        out = out + 2 * (-1j) ** q * sp_special.jv(q, R) * Tq
+    return out
+
+
+def test_apply_A_on_plane_waves_with_variable_coefficients(oracle_lib):
+    """A (u e^{i xi.x}) = -(b1 sigma_x i xi_x + b2 sigma_y i xi_y) u e^{i xi.x} pointwise,
+    for band-limited plane waves (spectral derivative exact), variable metric."""
+    nx, ny, ax, ay = 32, 16, 5.0, 4.0
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g11 = 1.0 + 0.3 * np.exp(-(X ** 2 + Y ** 2) / 4)
+    g22 = 1.0 + 0.2 * np.exp(-((X - 1) ** 2 + Y ** 2) / 3)
+    g00 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y + 1) ** 2) / 5)
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=0.0, g00=g00, g11=g11, g22=g22)
+    xs, ys = xi_vec(nx, ax), xi_vec(ny, ay)
+    qx, qy, u = 3, 13, np.array([0.7 - 0.1j, 0.2 + 0.4j])
+    e = np.exp(1j * xs[qx] * (X + ax) + 1j * ys[qy] * (Y + ay))
+    psi = np.stack([u[0] * e, u[1] * e])
+    got = oracle_lib.apply_A(prob, psi)
+    a1, a2 = np.sqrt(g00 / g11), np.sqrt(g00 / g22)
+    kx, ky = 1j * xs[qx], 1j * ys[qy]
+    # sigma_x u = (u2, u1), sigma_y u = (-i u2, i u1)
+    ref0 = -(a1 * kx * u[1] + a2 * ky * (-1j * u[1])) * e
+    ref1 = -(a1 * kx * u[0] + a2 * ky * (1j * u[0])) * e
+    assert np.abs(got[0] - ref0).max() <= 1e-12
+    assert np.abs(got[1] - ref1).max() <= 1e-12
+
+
+def test_apply_A_is_skew_adjoint_in_flat_space(oracle_lib):
+    n, a = 32, 6.0
+    prob = problem(oracle_lib, n, n, a, a)
+    f, g = W.random_state(n, n, 1), W.random_state(n, n, 2)
+    lhs = np.vdot(f, oracle_lib.apply_A(prob, g))
+    rhs = -np.vdot(oracle_lib.apply_A(prob, f), g)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_bessel_matches_scipy(oracle_lib):
+    for x, n in ((0.0, 4), (0.3, 10), (3.7, 20), (40.0, 60), (150.0, 200)):
+        assert np.abs(oracle_lib.bessel_j(x, n) - sp_special.jv(np.arange(n + 1), x)).max() <= 1e-14
+
+
+@pytest.mark.parametrize("family,order", [("taylor", 4), ("taylor", 7), ("chebyshev", 6),
+                                          ("chebyshev", 12)])
+def test_poly_scheme_per_mode_closed_form(oracle_lib, family, order):
+    """Constant metric: every plane wave is an eigenvector of A, so a step is
+    U (sum_q a_q P_q(dt A(xi))) U per mode."""
+    nx, ny, ax, ay = 32, 16, 6.0, 4.0
+    g = (1.3, 0.8, 1.1)
+    mass, c = 0.7, 1.0
+    modes = [(1, 0, (1.0, 0.5j)), (3, 14, (0.3 - 0.2j, 0.1)), (31, 5, (0.05, -0.4j)),
+             (16, 8, (0.02, 0.01))]
+    psi0 = W.plane_waves(nx, ny, ax, ay, modes)
+    G = [np.full((ny, nx), v) for v in g]
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=G[0], g11=G[1], g22=G[2])
+    dt, n = 0.03, 50
+    fam = oracle_lib.POLY_TAYLOR if family == "taylor" else oracle_lib.POLY_CHEBYSHEV
+    got = oracle_lib.run_poly(prob, psi0, dt, n, fam, order)
+    a1, a2 = c * np.sqrt(g[0] / g[1]), c * np.sqrt(g[0] / g[2])
+    me = mass * c * c * np.sqrt(g[0])
+    U = sla.expm(-1j * dt / 2 * me * SZ)
+    xs, ys = xi_vec(nx, ax), xi_vec(ny, ay)
+    R = dt * (a1 * np.pi / (2 * ax / nx) + a2 * np.pi / (2 * ay / ny))
+    X, Y = W.mesh(nx, ny, ax, ay)
+    ref = np.zeros_like(psi0)
+    for qx, qy, amps in modes:
+        M = -dt * (a1 * 1j * xs[qx] * SX + a2 * 1j * ys[qy] * SY)
+        T = U @ _poly_series(M, order, family, R) @ U
+        v = np.linalg.matrix_power(T, n) @ np.array(amps)
+        e = np.exp(1j * xs[qx] * (X + ax) + 1j * ys[qy] * (Y + ay))
+        ref[0] += v[0] * e
+        ref[1] += v[1] * e
+    assert W.rel_l2(got, ref) <= 1e-12
+
+
+def test_chebyshev_scheme_reaches_the_free_propagator(oracle_lib):
+    """Flat space, m = 0 (U = I): with enough terms the Chebyshev middle step is exp(dt A)
+    to rounding, so the scheme reproduces the exact free propagator exp(-i T H(xi))."""
+    n, a, T = 64, 10.0, 1.0
+    psi0 = W.wave_packet(n, n, a, a, 1.5, (1.0, -0.5))
+    psi0[1] = 0.5j * psi0[0]
+    prob = problem(oracle_lib, n, n, a, a, mass=0.0)
+    xs = xi_vec(n, a)
+    KX, KY = np.meshgrid(xs, xs, indexing="xy")
+    E = np.sqrt(KX ** 2 + KY ** 2) + 1e-300
+    h0, h1 = np.fft.fft2(psi0[0]), np.fft.fft2(psi0[1])
+    cs, sn = np.cos(T * E), np.sin(T * E) / E
+    r0 = cs * h0 - 1j * sn * ((KX - 1j * KY) * h1)
+    r1 = cs * h1 - 1j * sn * ((KX + 1j * KY) * h0)
+    exact = np.stack([np.fft.ifft2(r0), np.fft.ifft2(r1)])
+    dt = 0.1  # R = dt 2 pi / h = 2.0: 24 terms are far past convergence
+    got = oracle_lib.run_poly(prob, psi0, dt, int(round(T / dt)), oracle_lib.POLY_CHEBYSHEV, 24)
+    assert W.rel_l2(got, exact) <= 1e-12
