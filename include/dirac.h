@@ -60,7 +60,19 @@ typedef enum { DIRAC_C64 = 0, DIRAC_C128 = 1 } dirac_precision;
  * x sub-step twice over dt/2 around the y sub-step (U, x/2, y, x/2, U): the symmetric
  * (Strang) decomposition the paper's time discretization uses in flat space (Sec. 3,
  * eq. op_flat) carried over to the direction split; second order in time in flat space. The symmetric order costs three line passes per step. */
-typedef enum { DIRAC_SCHEME_II = 0, DIRAC_SCHEME_II_SYMMETRIC = 1 } dirac_scheme;
+typedef enum {
+  DIRAC_SCHEME_II = 0,
+  DIRAC_SCHEME_II_SYMMETRIC = 1,
+  /* The polynomial scheme (Sec. 4.2 eq. op_split_poly, Sec. 5 eq. poly): U, then the
+   * unsplit middle step psi <- sum_q a_q P_q(dt A) psi with A = -sum_j b^j sigma_j [[d_j]]
+   * (eq. alpha_form; b^j = a^j/S^j), then U. TAYLOR: a_q P_q(z) = z^q/q!. CHEBYSHEV:
+   * exp(dt A) = exp(-i H), H = i dt A, expanded as sum_q (2 - delta_q0) (-i)^q J_q(R)
+   * T_q(H/R) with R = dt sum_j max|b^j| pi/h_j. Explicit, hence only conditionally stable
+   * (Sec. 5: Taylor is usually unstable); the degree is set by dirac_set_poly_degree.
+   * Each term costs two derivative passes, a transpose and a pointwise combine. */
+  DIRAC_SCHEME_POLY_TAYLOR = 2,
+  DIRAC_SCHEME_POLY_CHEBYSHEV = 3
+} dirac_scheme;
 
 /* Spin connection Omega_j (Sec. 2.2). COVARIANT: Omega_j = 1/2 d_j ln(w a^j) with
  * w = sqrt(g11 g22 / g00) (= sqrt|g| g^00, the weight of the conserved norm, eq. l2gamma).
@@ -144,12 +156,17 @@ const char *dirac_last_error(const dirac_ctx *ctx);
 /* Releases the context and all its device memory. NULL is allowed. */
 void dirac_destroy(dirac_ctx *ctx);
 
-/* Selects the sub-step order of later dirac_step calls (dirac_scheme; the default is
+/* Selects the time-step scheme of later dirac_step calls (dirac_scheme; the default is
  * DIRAC_SCHEME_II). The symmetric order needs two more device arrays (x-pass multipliers
  * for dt/2 and U^2 in the normal layout), allocated on the next dirac_step. Contexts
- * with the symmetric order cannot join a batch (dirac_batch_submit returns
+ * with another scheme than DIRAC_SCHEME_II cannot join a batch (dirac_batch_submit returns
  * DIRAC_EUNSUPPORTED). DIRAC_EINVAL for other values. */
 dirac_status dirac_set_scheme(dirac_ctx *ctx, int scheme);
+
+/* Degree N_p of the polynomial schemes' middle step (1..256; default 8). The polynomial
+ * schemes use three more state-sized device arrays, allocated on the next dirac_step.
+ * DIRAC_EINVAL for other values. */
+dirac_status dirac_set_poly_degree(dirac_ctx *ctx, int degree);
 
 /* CTA shape of the two fused passes (each pass: FFT along a line, k-space multiply,
  * inverse FFT, combine, transposed store): about 256 or 512 threads per CTA for that

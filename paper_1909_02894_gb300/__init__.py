@@ -23,6 +23,7 @@ STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_EINVAL", 2: "DIRAC_ENOMEM", 3: "DIRAC_E
 DIRAC_C64, DIRAC_C128 = 0, 1
 DIRAC_CONN_COVARIANT, DIRAC_CONN_PAPER_2D, DIRAC_CONN_NONE = 0, 1, 2
 DIRAC_SCHEME_II, DIRAC_SCHEME_II_SYMMETRIC = 0, 1
+DIRAC_SCHEME_POLY_TAYLOR, DIRAC_SCHEME_POLY_CHEBYSHEV = 2, 3
 
 # Every symbol the header declares; the CPU tests check that the library exports them.
 ABI_SYMBOLS = (
@@ -30,6 +31,7 @@ ABI_SYMBOLS = (
     "dirac_observables", "dirac_synchronize", "dirac_last_error", "dirac_destroy",
     "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc", "dirac_footprint_bytes",
     "dirac_autotune", "dirac_test_timeout_next_step", "dirac_set_scheme",
+    "dirac_set_poly_degree",
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
@@ -97,6 +99,7 @@ def lib():
         L.dirac_destroy.restype = None
         L.dirac_set_launch.argtypes = [vp, i, i]
         L.dirac_set_scheme.argtypes = [vp, i]
+        L.dirac_set_poly_degree.argtypes = [vp, i]
         L.dirac_launch_count.argtypes = [vp]
         L.dirac_launch_count.restype = l
         L.dirac_norms_noalloc.argtypes = [vp, vp, i, i, d, d, vp, vp]
@@ -222,6 +225,10 @@ def dirac_set_scheme(ctx, scheme: int):
     _check(lib().dirac_set_scheme(ctx, int(scheme)), ctx)
 
 
+def dirac_set_poly_degree(ctx, degree: int):
+    _check(lib().dirac_set_poly_degree(ctx, int(degree)), ctx)
+
+
 def dirac_launch_count(ctx) -> int:
     return int(lib().dirac_launch_count(ctx))
 
@@ -322,7 +329,7 @@ class Simulation:
     """Owns one context; marshalling only (same calls as the C ABI)."""
 
     def __init__(self, workload, precision=DIRAC_C64, stream=None, conn=None,
-                 scheme=DIRAC_SCHEME_II):
+                 scheme=DIRAC_SCHEME_II, poly_degree=None):
         w = workload
         self.nx, self.ny = w.nx, w.ny
         self.ctx = dirac_create(
@@ -332,6 +339,8 @@ class Simulation:
             sigma0=w.sigma0, theta=w.theta, precision=precision, stream=stream)
         if scheme != DIRAC_SCHEME_II:
             dirac_set_scheme(self.ctx, scheme)
+        if poly_degree is not None:
+            dirac_set_poly_degree(self.ctx, poly_degree)
 
     def set_state(self, psi):
         dirac_set_state(self.ctx, psi)

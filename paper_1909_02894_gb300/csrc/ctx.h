@@ -33,6 +33,9 @@ struct dirac_ctx {
   double *partials = nullptr, *result = nullptr, *density = nullptr;
 
   int scheme = DIRAC_SCHEME_II;
+  int poly_degree = 8;
+  void* pool[3] = {nullptr, nullptr, nullptr};  // polynomial schemes: term buffers
+  double bmax[2] = {-1.0, -1.0};                // max |b1|, |b2| (Chebyshev bound)
   void *mult_xh = nullptr, *u2_n = nullptr;  // symmetric order: x multipliers at dt/2,
                                              // U^2 in the normal layout
   int* d_err = nullptr;       // device error flag written by bounded waits

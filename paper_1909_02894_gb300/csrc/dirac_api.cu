@@ -93,15 +93,15 @@ template <typename T>
 static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
   cudaStream_t st = ctx->stream;
   const bool sym = ctx->scheme == DIRAC_SCHEME_II_SYMMETRIC;
-  if (sym) {
-    if (!ctx->mult_xh) CK(dalloc(ctx, &ctx->mult_xh, ctx->nx * sizeof(Q4<T>)), "allocate tables");
-    if (!ctx->u_identity && !ctx->u2_n)
-      CK(dalloc(ctx, &ctx->u2_n, npts(ctx) * sizeof(Q4<T>)), "allocate half-step");
-  }
+  const bool need_u2n = ctx->scheme != DIRAC_SCHEME_II;  // U^2 applied in the normal layout
+  if (sym && !ctx->mult_xh)
+    CK(dalloc(ctx, &ctx->mult_xh, ctx->nx * sizeof(Q4<T>)), "allocate tables");
+  if (need_u2n && !ctx->u_identity && !ctx->u2_n)
+    CK(dalloc(ctx, &ctx->u2_n, npts(ctx) * sizeof(Q4<T>)), "allocate half-step");
   if (!ctx->u_identity) {
     CK(launch_halfstep<T>(ctx->a1, ctx->a2, ctx->meff, ctx->omx, ctx->omy, ctx->nx, ctx->ny, dt,
                           (Q4<T>*)ctx->u_n, (Q4<T>*)ctx->u_t, (Q4<T>*)ctx->u2_t,
-                          sym ? (Q4<T>*)ctx->u2_n : nullptr, st),
+                          need_u2n ? (Q4<T>*)ctx->u2_n : nullptr, st),
        "half-step matrices");
     ctx->launches += 1;
   }
@@ -161,6 +161,127 @@ static dirac_status step_symmetric(dirac_ctx* ctx, long n) {
   return DIRAC_OK;
 }
 
+// out = alpha S(in) + beta prev, acc += gamma out, with S(in) = sum_j b^j sigma_j [[d_j]] in
+// (so dt A = -dt S): x derivative (row pass, rows back in place), transpose, y derivative
+// (transposed store back to rows), pointwise combine. psiT, scratch1, scratch2 are scratch.
+template <typename T>
+static dirac_status unsplit_apply(dirac_ctx* ctx, const void* in, void* out, double ar,
+                                  double ai, const void* prev, double beta, double gr,
+                                  double gi, void* acc) {
+  cudaStream_t st = ctx->stream;
+  LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
+  ax.in = (const Q4<T>*)in;
+  ax.out = (Q4<T>*)ctx->scratch1;
+  ax.mult = (const Q4<T>*)ctx->dmult_x;
+  ax.store_normal = 1;
+  CK(launch_line_pass<T>(ax, MODE_DERIV, 0, st), "x derivative");
+  CK(launch_transpose<T>((const Q4<T>*)in, (Q4<T>*)ctx->psiT, ctx->ny, ctx->nx, st), "transpose");
+  ay.in = (const Q4<T>*)ctx->psiT;
+  ay.out = (Q4<T>*)ctx->scratch2;
+  ay.mult = (const Q4<T>*)ctx->dmult_y;
+  CK(launch_line_pass<T>(ay, MODE_DERIV, 0, st), "y derivative");
+  CK(launch_unsplit_combine<T>((const Q4<T>*)ctx->scratch1, (const Q4<T>*)ctx->scratch2, ctx->a1,
+                               ctx->a2, ctx->sxinv, ctx->syinv, ctx->nx, ctx->ny, ar, ai,
+                               (const Q4<T>*)prev, beta, gr, gi, (Q4<T>*)out, (Q4<T>*)acc, st),
+     "combine");
+  ctx->launches += 4;
+  return DIRAC_OK;
+}
+
+#define CKS(x)                       \
+  do {                               \
+    dirac_status s_ = (x);           \
+    if (s_ != DIRAC_OK) return s_;   \
+  } while (0)
+
+// The polynomial scheme (eq. poly): U, the middle step, U per step, with U^2 between
+// consecutive steps of a call. Four state-sized buffers (the state and pool[0..2]) rotate:
+// the middle step's sum becomes the new state.
+template <typename T>
+static dirac_status step_poly(dirac_ctx* ctx, long n, double dt) {
+  cudaStream_t st = ctx->stream;
+  const size_t np = npts(ctx), bytes = np * sizeof(Q4<T>);
+  for (void*& p : ctx->pool)
+    if (!p) CK(dalloc(ctx, &p, bytes), "allocate polynomial terms");
+  if (!ctx->scratch1) CK(dalloc(ctx, &ctx->scratch1, bytes), "scratch");
+  if (!ctx->scratch2) CK(dalloc(ctx, &ctx->scratch2, bytes), "scratch");
+  const int N = ctx->poly_degree;
+  const bool cheb = ctx->scheme == DIRAC_SCHEME_POLY_CHEBYSHEV;
+  std::vector<double> jq(N + 1, 0.0);
+  double R = 0.0;
+  if (cheb) {
+    if (ctx->bmax[0] < 0.0) {  // max |b^j| over the grid, once per context
+      const int nb = 256;
+      double* part = nullptr;
+      CK(dalloc(ctx, (void**)&part, 2 * nb * sizeof(double)), "scratch");
+      CK(launch_max_b(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, ctx->nx, ctx->ny, part, nb, st),
+         "max b");
+      std::vector<double> h(2 * nb);
+      CK(cudaMemcpyAsync(h.data(), part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st),
+         "max b");
+      CK(cudaStreamSynchronize(st), "max b");
+      ctx->bmax[0] = ctx->bmax[1] = 0.0;
+      for (int b = 0; b < nb; ++b) {
+        ctx->bmax[0] = fmax(ctx->bmax[0], h[2 * b]);
+        ctx->bmax[1] = fmax(ctx->bmax[1], h[2 * b + 1]);
+      }
+      ctx->launches += 1;
+    }
+    const double hx = 2.0 * ctx->ax / ctx->nx, hy = 2.0 * ctx->ay / ctx->ny;
+    R = dt * (ctx->bmax[0] * M_PI / hx + ctx->bmax[1] * M_PI / hy);
+    if (!(R > 0.0) || !bessel_j_series(R, N, jq.data()))
+      return fail(ctx, DIRAC_EINVAL, "no Chebyshev bound for this grid and dt");
+  }
+  for (long s = 0; s < n; ++s) {
+    if (!ctx->u_identity && s == 0) {
+      CK(launch_apply_u<T>((Q4<T>*)ctx->psi, (const Q4<T>*)ctx->u_n, np, st), "half step");
+      ctx->launches += 1;
+    }
+    void* bufs[4] = {ctx->psi, ctx->pool[0], ctx->pool[1], ctx->pool[2]};
+    void* acc = bufs[3];
+    if (!cheb) {
+      // acc = sum_q (dt A)^q / q! psi; (dt/q) A t = -(dt/q) S(t)
+      CK(cudaMemcpyAsync(acc, bufs[0], bytes, cudaMemcpyDeviceToDevice, st), "copy");
+      void *cur = bufs[0], *nxt = bufs[1], *spare = bufs[2];
+      for (int q = 1; q <= N; ++q) {
+        CKS(unsplit_apply<T>(ctx, cur, nxt, -dt / q, 0.0, nullptr, 0.0, 1.0, 0.0, acc));
+        cur = nxt;
+        nxt = (cur == bufs[1]) ? spare : bufs[1];
+      }
+    } else {
+      // phi_0 = psi, phi_1 = B phi_0, phi_{q+1} = 2 B phi_q - phi_{q-1} with
+      // B = (i dt / R) A = -(i dt / R) S; acc = sum_q (2 - delta_q0) (-i)^q J_q(R) phi_q
+      CK(launch_scale<T>((Q4<T>*)acc, (const Q4<T>*)bufs[0], jq[0], 0.0, np, st), "scale");
+      ctx->launches += 1;
+      static const double pr[4] = {1.0, 0.0, -1.0, 0.0}, pi_[4] = {0.0, -1.0, 0.0, 1.0};
+      void *prev = bufs[0], *cur = bufs[1], *spare = bufs[2];
+      if (N >= 1)
+        CKS(unsplit_apply<T>(ctx, prev, cur, 0.0, -dt / R, nullptr, 0.0, 2.0 * pr[1] * jq[1],
+                             2.0 * pi_[1] * jq[1], acc));
+      for (int q = 2; q <= N; ++q) {
+        CKS(unsplit_apply<T>(ctx, cur, spare, 0.0, -2.0 * dt / R, prev, -1.0,
+                             2.0 * pr[q & 3] * jq[q], 2.0 * pi_[q & 3] * jq[q], acc));
+        void* t = prev;
+        prev = cur;
+        cur = spare;
+        spare = t;
+      }
+    }
+    // the sum is the new state; the other three buffers become the pool
+    int k = 0;
+    for (void* b : bufs)
+      if (b != acc) ctx->pool[k++] = b;
+    ctx->psi = acc;
+    if (!ctx->u_identity) {
+      CK(launch_apply_u<T>((Q4<T>*)ctx->psi,
+                           (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n), np, st),
+         "half step");
+      ctx->launches += 1;
+    }
+  }
+  return DIRAC_OK;
+}
+
 template <typename T>
 static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   if (dt != ctx->dt_cached) {
@@ -168,6 +289,8 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
     if (s != DIRAC_OK) return s;
   }
   if (ctx->scheme == DIRAC_SCHEME_II_SYMMETRIC) return step_symmetric<T>(ctx, n);
+  if (ctx->scheme == DIRAC_SCHEME_POLY_TAYLOR || ctx->scheme == DIRAC_SCHEME_POLY_CHEBYSHEV)
+    return step_poly<T>(ctx, n, dt);
   LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
   ax.in = (const Q4<T>*)ctx->psi;
   ax.out = (Q4<T>*)ctx->psiT;
@@ -612,12 +735,19 @@ void dirac_destroy(dirac_ctx* ctx) {
 
 dirac_status dirac_set_scheme(dirac_ctx* ctx, int scheme) {
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
-  if (scheme != DIRAC_SCHEME_II && scheme != DIRAC_SCHEME_II_SYMMETRIC)
-    return fail(ctx, DIRAC_EINVAL, "scheme must be DIRAC_SCHEME_II or DIRAC_SCHEME_II_SYMMETRIC");
+  if (scheme < DIRAC_SCHEME_II || scheme > DIRAC_SCHEME_POLY_CHEBYSHEV)
+    return fail(ctx, DIRAC_EINVAL, "unknown scheme");
   if (scheme != ctx->scheme) {
     ctx->scheme = scheme;
     ctx->dt_cached = 0.0;  // the tables of the new order are made on the next step
   }
+  return DIRAC_OK;
+}
+
+dirac_status dirac_set_poly_degree(dirac_ctx* ctx, int degree) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (degree < 1 || degree > 256) return fail(ctx, DIRAC_EINVAL, "degree must be 1..256");
+  ctx->poly_degree = degree;
   return DIRAC_OK;
 }
 

@@ -58,6 +58,29 @@ cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream
 template <typename T>
 cudaError_t launch_deriv_mult(int n, double a, Q4<T>* mult, cudaStream_t st);
 
+// ---- unsplit polynomial scheme (unsplit.cu)
+// psi <- U psi at every point (normal layout).
+template <typename T>
+cudaError_t launch_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n, cudaStream_t st);
+// out = alpha (b1 sigma_x dx + b2 sigma_y dy) + beta prev (prev may be null); acc +=
+// gamma out (acc may be null); b^j = a^j / S^j from the FP64 fields; all normal layout.
+template <typename T>
+cudaError_t launch_unsplit_combine(const Q4<T>* dx, const Q4<T>* dy, const double* a1,
+                                   const double* a2, const double* sxinv, const double* syinv,
+                                   int nx, int ny, double ar, double ai, const Q4<T>* prev,
+                                   double beta, double gr, double gi, Q4<T>* out, Q4<T>* acc,
+                                   cudaStream_t st);
+// out = c in.
+template <typename T>
+cudaError_t launch_scale(Q4<T>* out, const Q4<T>* in, double cr, double ci, size_t n,
+                         cudaStream_t st);
+// Per-block maxima of |b1|, |b2| into partials[2 * n_blocks].
+cudaError_t launch_max_b(const double* a1, const double* a2, const double* sxinv,
+                         const double* syinv, int nx, int ny, double* partials,
+                         int n_blocks, cudaStream_t st);
+// J_0(x) .. J_n(x) into out[0..n] (host, FP64); false for x < 0 or n < 0.
+bool bessel_j_series(double x, int n, double* out);
+
 // Tiled transpose of a [rows][cols] array of Q4<T> into [cols][rows].
 template <typename T>
 cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cudaStream_t st);

@@ -65,8 +65,8 @@ struct LinePassArgs {
   int inst_capacity;        // batched launch: table entries (host side, sizes the grid)
   unsigned test_extra_tx;   // test hook: bytes a bulk copy never delivers (0 normally);
                             // makes the persistent pass's bounded wait run out
-  int store_normal;         // step mode: 0 = out is [L][n_lines] (transposed store),
-                            // 1 = out is [n_lines][L] like `in` (out must not alias in)
+  int store_normal;         // 0 = out is [L][n_lines] (transposed store), 1 = out is
+                            // [n_lines][L] like `in` (out must not alias in)
 };
 
 // Batched launches: a block (or group) of lines belongs to instance `k`; take that
@@ -504,7 +504,8 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       if (a.store_normal) reinterpret_cast<Cx<T>*>(a.out)[2 * gi + c] = o;
       else my_stage[2 * i] = o;
     } else {
-      my_stage[2 * i] = v[m];
+      if (a.store_normal) reinterpret_cast<Cx<T>*>(a.out)[2 * (row + i) + c] = v[m];
+      else my_stage[2 * i] = v[m];
     }
   }
 
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
   const int i0 = rank * ROWS;
   constexpr int HALF = Gm::NIT / 2;
   // (a normal-layout store happened in the epilogue)
-  if (!(MODE == MODE_STEP && a.store_normal)) {
+  if (!a.store_normal) {
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     Q4<T> val[HALF];

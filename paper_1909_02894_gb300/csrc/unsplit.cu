@@ -1,0 +1,171 @@
+// Pointwise kernels of the unsplit polynomial scheme (Sec. 4.2 eq. op_split_poly, Sec. 5
+// eq. poly): the middle step applies sum_q a_q P_q(dt A) with
+//   A psi = - sum_j b^j sigma_j [[d_j]] psi,   b^j = a^j / S^j (Sec. 3),
+// where the spectral derivatives come from the derivative-mode line passes and the rest
+// is one combine kernel per operator application.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "internal.h"
+
+namespace dgb {
+
+namespace {
+constexpr int TPB = 256;
+unsigned blocks_for(size_t n) { return (unsigned)((n + TPB - 1) / TPB); }
+}  // namespace
+
+// psi <- U psi at every point of the normal layout
+template <typename T>
+__global__ void k_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) psi[k] = apply_u(u[k], psi[k]);
+}
+
+// S = b1 sigma_x dx + b2 sigma_y dy with sigma_x (u, v) = (v, u), sigma_y (u, v) =
+// (-i v, i u); out = alpha S + beta prev; acc += gamma out.
+template <typename T>
+__global__ void k_unsplit_combine(const Q4<T>* dx, const Q4<T>* dy, const double* a1,
+                                  const double* a2, const double* sxinv, const double* syinv,
+                                  int nx, int ny, T ar, T ai, const Q4<T>* prev, T beta, T gr,
+                                  T gi, Q4<T>* out, Q4<T>* acc) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (size_t)nx * ny) return;
+  const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+  const T b1 = (T)(a1[k] * sxinv[i]), b2 = (T)(a2[k] * syinv[j]);
+  const Q4<T> x = dx[k], y = dy[k];
+  const T s1r = b1 * x.z + b2 * y.w, s1i = b1 * x.w - b2 * y.z;
+  const T s2r = b1 * x.x - b2 * y.y, s2i = b1 * x.y + b2 * y.x;
+  Q4<T> o = {ar * s1r - ai * s1i, ar * s1i + ai * s1r, ar * s2r - ai * s2i, ar * s2i + ai * s2r};
+  if (prev) {
+    const Q4<T> p = prev[k];
+    o.x += beta * p.x;
+    o.y += beta * p.y;
+    o.z += beta * p.z;
+    o.w += beta * p.w;
+  }
+  out[k] = o;
+  if (acc) {
+    Q4<T> s = acc[k];
+    s.x += gr * o.x - gi * o.y;
+    s.y += gr * o.y + gi * o.x;
+    s.z += gr * o.z - gi * o.w;
+    s.w += gr * o.w + gi * o.z;
+    acc[k] = s;
+  }
+}
+
+// out = c in (complex c)
+template <typename T>
+__global__ void k_scale(Q4<T>* out, const Q4<T>* in, T cr, T ci, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const Q4<T> v = in[k];
+  out[k] = {cr * v.x - ci * v.y, cr * v.y + ci * v.x, cr * v.z - ci * v.w, cr * v.w + ci * v.z};
+}
+
+// Per-block maxima of |b1| and |b2| (grid-stride), partials[2 b], partials[2 b + 1].
+__global__ void k_max_b(const double* a1, const double* a2, const double* sxinv,
+                        const double* syinv, int nx, int ny, double* partials) {
+  __shared__ double m1[TPB], m2[TPB];
+  double x1 = 0.0, x2 = 0.0;
+  const size_t n = (size_t)nx * ny;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
+    x1 = fmax(x1, fabs(a1[k] * sxinv[i]));
+    x2 = fmax(x2, fabs(a2[k] * syinv[j]));
+  }
+  m1[threadIdx.x] = x1;
+  m2[threadIdx.x] = x2;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      m1[threadIdx.x] = fmax(m1[threadIdx.x], m1[threadIdx.x + s]);
+      m2[threadIdx.x] = fmax(m2[threadIdx.x], m2[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = m1[0];
+    partials[2 * blockIdx.x + 1] = m2[0];
+  }
+}
+
+template <typename T>
+cudaError_t launch_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n, cudaStream_t st) {
+  k_apply_u<T><<<blocks_for(n), TPB, 0, st>>>(psi, u, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_unsplit_combine(const Q4<T>* dx, const Q4<T>* dy, const double* a1,
+                                   const double* a2, const double* sxinv, const double* syinv,
+                                   int nx, int ny, double ar, double ai, const Q4<T>* prev,
+                                   double beta, double gr, double gi, Q4<T>* out, Q4<T>* acc,
+                                   cudaStream_t st) {
+  k_unsplit_combine<T><<<blocks_for((size_t)nx * ny), TPB, 0, st>>>(
+      dx, dy, a1, a2, sxinv, syinv, nx, ny, (T)ar, (T)ai, prev, (T)beta, (T)gr, (T)gi, out, acc);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scale(Q4<T>* out, const Q4<T>* in, double cr, double ci, size_t n,
+                         cudaStream_t st) {
+  k_scale<T><<<blocks_for(n), TPB, 0, st>>>(out, in, (T)cr, (T)ci, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_b(const double* a1, const double* a2, const double* sxinv,
+                         const double* syinv, int nx, int ny, double* partials,
+                         int n_blocks, cudaStream_t st) {
+  k_max_b<<<n_blocks, TPB, 0, st>>>(a1, a2, sxinv, syinv, nx, ny, partials);
+  return cudaGetLastError();
+}
+
+// Bessel functions J_0(x) .. J_n(x), x >= 0, by downward recurrence from an order well
+// above max(n, x) (where the minimal solution dominates), J_{k-1} = (2k/x) J_k - J_{k+1},
+// normalised by the Neumann sum J_0 + 2 (J_2 + J_4 + ...) = 1. Returns false for bad input.
+bool bessel_j_series(double x, int n, double* out) {
+  if (!(x >= 0.0) || n < 0) return false;
+  for (int k = 0; k <= n; ++k) out[k] = 0.0;
+  if (x == 0.0) {
+    out[0] = 1.0;
+    return true;
+  }
+  const double big = fmax((double)n, x);
+  int top = (int)(big + 50.0 + 6.0 * sqrt(big));
+  if (top % 2) ++top;
+  double hi = 0.0, mid = 1e-300, norm = 0.0;
+  for (int k = top; k > 0; --k) {
+    const double lo = 2.0 * k / x * mid - hi;  // J_{k-1} (unnormalised)
+    hi = mid;
+    mid = lo;
+    const int idx = k - 1;
+    if (fabs(mid) > 1e200) {
+      hi *= 1e-200;
+      mid *= 1e-200;
+      norm *= 1e-200;
+      for (int t = 0; t <= n; ++t) out[t] *= 1e-200;
+    }
+    if (idx <= n) out[idx] = mid;
+    if (idx > 0 && idx % 2 == 0) norm += 2.0 * mid;
+  }
+  norm += mid;
+  for (int k = 0; k <= n; ++k) out[k] /= norm;
+  return true;
+}
+
+#define INST(T)                                                                              \
+  template cudaError_t launch_apply_u<T>(Q4<T>*, const Q4<T>*, size_t, cudaStream_t);        \
+  template cudaError_t launch_unsplit_combine<T>(                                            \
+      const Q4<T>*, const Q4<T>*, const double*, const double*, const double*, const double*, \
+      int, int, double, double, const Q4<T>*, double, double, double, Q4<T>*, Q4<T>*,       \
+      cudaStream_t);                                                                         \
+  template cudaError_t launch_scale<T>(Q4<T>*, const Q4<T>*, double, double, size_t,         \
+                                       cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace dgb
