@@ -199,16 +199,23 @@ def run_reference(args, wl_name):
     return 0
 
 
-def cpu_baseline(w, scheme=0):
+def cpu_baseline(w, scheme="printed", degree=8):
     """Oracle timing on a bounded sample of the same workload (about 10-30 s of CPU)."""
     import oracle
 
     oracle.build()
     prob = oracle.Problem.from_workload(w)
+
+    def run(n):
+        if scheme in ("taylor", "chebyshev"):
+            fam = oracle.POLY_TAYLOR if scheme == "taylor" else oracle.POLY_CHEBYSHEV
+            return oracle.run_poly(prob, w.psi0, w.dt, n, fam, degree)
+        return oracle.run(prob, w.psi0, w.dt, n, scheme=1 if scheme == "symmetric" else 0)
+
     t0 = time.perf_counter()
-    oracle.run(prob, w.psi0, w.dt, 1, scheme=scheme)
+    run(1)
     t1 = time.perf_counter()
-    oracle.run(prob, w.psi0, w.dt, 2, scheme=scheme)
+    run(2)
     t2 = time.perf_counter()
     per_step = max((t2 - t1) - (t1 - t0), 1e-9)
     return {"value": w.nx * w.ny / per_step, "unit": UNIT, "cores": oracle.threads(),
@@ -367,8 +374,11 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--sustainable-rate", type=float, default=4.0)
     ap.add_argument("--sustainable-seconds", type=float, default=20.0)
-    ap.add_argument("--scheme", default="printed", choices=["printed", "symmetric"],
-                    help="sub-step order: printed (x, y) or symmetric (x/2, y, x/2)")
+    ap.add_argument("--scheme", default="printed",
+                    choices=["printed", "symmetric", "taylor", "chebyshev"],
+                    help="Scheme II (printed x, y or symmetric x/2, y, x/2 order) or the "
+                         "polynomial scheme with a Taylor or Chebyshev middle step")
+    ap.add_argument("--poly-degree", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args, args.workload)
@@ -390,15 +400,26 @@ def main():
     w, prec_name, bytes_pt = workload(args.workload)
     prec = D.DIRAC_C64 if prec_name == "c64" else D.DIRAC_C128
     symmetric = args.scheme == "symmetric"
+    poly = args.scheme in ("taylor", "chebyshev")
     passes = 3 if symmetric else 2
+    scheme_id = {"printed": D.DIRAC_SCHEME_II, "symmetric": D.DIRAC_SCHEME_II_SYMMETRIC,
+                 "taylor": D.DIRAC_SCHEME_POLY_TAYLOR,
+                 "chebyshev": D.DIRAC_SCHEME_POLY_CHEBYSHEV}[args.scheme]
     if symmetric:
         # three sweeps of psi, b - 1 read in each, U^2 once: 124 B (complex64)
         bytes_pt = bytes_pt // 88 * 124
+    if poly:
+        # per term: x-derivative pass, transpose, y-derivative pass (each a read and a write
+        # of a state array), combine (dx, dy, FP64 a1 a2, previous term for Chebyshev,
+        # output, accumulator read and write); per step: U^2 on the state, the first copy
+        s = bytes_pt // 88 * 16  # bytes of one state point
+        term = 6 * s + (2 * s + 16 + (s if args.scheme == "chebyshev" else 0) + s + 2 * s)
+        bytes_pt = args.poly_degree * term + 2 * s + 16 + 2 * s
     # A dedicated stream: the default stream's handle is 0, which the ABI reads as
     # "create a private stream", and events must be recorded where the kernels run.
     stream = torch.cuda.Stream()
-    sim = D.Simulation(w, precision=prec, stream=stream.cuda_stream,
-                       scheme=D.DIRAC_SCHEME_II_SYMMETRIC if symmetric else D.DIRAC_SCHEME_II)
+    sim = D.Simulation(w, precision=prec, stream=stream.cuda_stream, scheme=scheme_id,
+                       poly_degree=args.poly_degree if poly else None)
     sim.set_state(w.psi0)
     pts = w.nx * w.ny
     warm = max(3, args.warmup)
@@ -435,7 +456,9 @@ def main():
     per_launch_s = ms * 1e-3 / max(1, launches)
     alg_bytes_launch = bytes_pt * pts / float(passes)
     achieved = alg_bytes_launch / per_launch_s / 1e9
-    traffic = None if symmetric else ncu_traffic(args.workload)
+    if poly:  # many kernels per step: the whole step against the roofline
+        achieved = bytes_pt * pts / (ms * 1e-3 / args.steps) / 1e9
+    traffic = None if (symmetric or poly) else ncu_traffic(args.workload)
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -464,21 +487,27 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == D.DIRAC_C64 else "f64", "data": "synthetic",
             "config": {"workload": w.name, "precision": prec_name, "grid": [w.nx, w.ny],
-                       "scheme": "Scheme II, symmetric x/2-y-x/2" if symmetric
-                       else "Scheme II (x, y)",
+                       "scheme": {"printed": "Scheme II (x, y)",
+                                  "symmetric": "Scheme II, symmetric x/2-y-x/2",
+                                  "taylor": f"polynomial, Taylor degree {args.poly_degree}",
+                                  "chebyshev": f"polynomial, Chebyshev degree {args.poly_degree}",
+                                  }[args.scheme],
                        "dt": w.dt, "absorber": w.pml_width_x, "parallelism": "replicas",
                        "l2": "inputs larger than L2 (no flush)"
                        if bytes_pt * pts > L2_BYTES else "working set fits L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind, "kernel": kernel_name(w, prec_name),
+                         "peak_source": peak_kind,
+                         "kernel": "whole step (derivative passes, transposes, combines)"
+                         if poly else kernel_name(w, prec_name),
                          "algorithmic_bytes_per_point_step": bytes_pt},
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
             "e2e": e2e,
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, scheme=1 if symmetric else 0)
+            line["cpu_baseline"] = cpu_baseline(w, scheme=args.scheme,
+                                                degree=args.poly_degree)
         print(json.dumps(line))
     sim.close()
     if world > 1:
