@@ -69,6 +69,8 @@ def lib():
         L.oracle_apply_A.argtypes = [P, dp, dp, dp, dp, dp]
         L.oracle_bessel_j.argtypes = [C.c_double, C.c_int, dp]
         L.oracle_run_poly.argtypes = [P, dp, dp, dp, C.c_double, C.c_long, C.c_int, C.c_int, dp]
+        L.oracle_run_cn.argtypes = [P, dp, dp, dp, C.c_double, C.c_long, C.c_double, C.c_int,
+                                    C.c_int, C.POINTER(C.c_long), dp]
         L.oracle_modes_evolve_scheme.argtypes = [P, C.c_double, C.c_double, C.c_double,
                                                  C.c_double, C.c_long, C.c_int, C.c_int, dp,
                                                  dp, dp, C.c_int, dp, dp, dp]
@@ -76,7 +78,7 @@ def lib():
         for f in ("oracle_fft", "oracle_deriv", "oracle_coefficients", "oracle_half_step",
                   "oracle_run", "oracle_observables", "oracle_modes_evolve", "oracle_threads",
                   "oracle_run_scheme", "oracle_modes_evolve_scheme", "oracle_apply_A",
-                  "oracle_bessel_j", "oracle_run_poly"):
+                  "oracle_bessel_j", "oracle_run_poly", "oracle_run_cn"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -210,6 +212,19 @@ def run_poly(prob: Problem, psi, dt, n_steps, family=POLY_CHEBYSHEV, order=8):
                                  float(dt), int(n_steps), int(family), int(order), _ptr(psi)),
            "run_poly")
     return psi
+
+
+def run_cn(prob: Problem, psi, dt, n_steps, tol=1e-13, restart=30, max_restarts=100):
+    """n_steps of Scheme I (Crank-Nicolson, GMRES); returns (psi, Arnoldi steps)."""
+    psi = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    it = C.c_long(0)
+    rc = lib().oracle_run_cn(C.byref(prob._params()), *[_ptr(x) for x in prob._g()], float(dt),
+                             int(n_steps), float(tol), int(restart), int(max_restarts),
+                             C.byref(it), _ptr(psi))
+    if rc == -2:
+        raise RuntimeError("oracle GMRES did not converge")
+    _check(rc, "run_cn")
+    return psi, it.value
 
 
 def observables(prob: Problem, psi, with_density=False):

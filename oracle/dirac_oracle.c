@@ -521,6 +521,118 @@ int oracle_run_poly(const oracle_params *p, const double *g00, const double *g11
 }
 
 /* ---------------------------------------------------------------------------------
+ * Scheme I (Sec. 5.1 eq. cn): G psi* = G~ psi, G = I - (dt/2) A, G~ = I + (dt/2) A,
+ * solved by restarted GMRES with modified Gram-Schmidt and Givens rotations.
+ * ------------------------------------------------------------------------------- */
+static cplx zdot(const cplx *a, const cplx *b, size_t n) { /* sum conj(a) b */
+  cplx s = 0.0;
+  for (size_t k = 0; k < n; k++) s += conj(a[k]) * b[k];
+  return s;
+}
+
+/* out = in + sgn (dt/2) A in */
+static void apply_G(const oracle_params *p, const cplx *b1, const cplx *b2, double sgn,
+                    double dt, const cplx *in, cplx *out, cplx *d) {
+  const size_t n2 = 2 * (size_t)p->nx * p->ny;
+  apply_A(p, b1, b2, in, out, d);
+  for (size_t k = 0; k < n2; k++) out[k] = in[k] + sgn * 0.5 * dt * out[k];
+}
+
+static int cn_solve(const oracle_params *p, const cplx *b1, const cplx *b2, double dt,
+                    const cplx *rhs, cplx *x, double tol, int m, int max_restarts,
+                    long *iters) {
+  const size_t n2 = 2 * (size_t)p->nx * p->ny;
+  cplx *V = malloc(sizeof(cplx) * n2 * (size_t)(m + 1));
+  cplx *w = malloc(sizeof(cplx) * n2), *d = malloc(sizeof(cplx) * n2);
+  cplx *H = calloc((size_t)(m + 1) * m, sizeof(cplx));
+  cplx *cs = malloc(sizeof(cplx) * m), *sn = malloc(sizeof(cplx) * m);
+  cplx *g = malloc(sizeof(cplx) * (m + 1)), *y = malloc(sizeof(cplx) * m);
+  const double bnorm = sqrt(creal(zdot(rhs, rhs, n2)));
+  int rc = -2;
+  for (int cycle = 0; cycle <= max_restarts; cycle++) {
+    apply_G(p, b1, b2, -1.0, dt, x, w, d);
+    for (size_t k = 0; k < n2; k++) w[k] = rhs[k] - w[k];
+    const double beta = sqrt(creal(zdot(w, w, n2)));
+    if (beta <= tol * bnorm || beta == 0.0) {
+      rc = 0;
+      break;
+    }
+    if (cycle == max_restarts) break;
+    for (size_t k = 0; k < n2; k++) V[k] = w[k] / beta;
+    for (int i = 0; i <= m; i++) g[i] = 0.0;
+    g[0] = beta;
+    int kdim = 0;
+    for (int j = 0; j < m; j++) {
+      cplx *vj = V + (size_t)j * n2, *vn = V + (size_t)(j + 1) * n2;
+      apply_G(p, b1, b2, -1.0, dt, vj, vn, d);
+      for (int i = 0; i <= j; i++) {
+        const cplx *vi = V + (size_t)i * n2;
+        const cplx h = zdot(vi, vn, n2);
+        H[(size_t)i * m + j] = h;
+        for (size_t k = 0; k < n2; k++) vn[k] -= h * vi[k];
+      }
+      const double hn = sqrt(creal(zdot(vn, vn, n2)));
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0)
+        for (size_t k = 0; k < n2; k++) vn[k] /= hn;
+      /* earlier rotations on column j, then a new one zeroing H[j+1][j] */
+      for (int i = 0; i < j; i++) {
+        const cplx a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = conj(cs[i]) * a + conj(sn[i]) * b;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+      }
+      const cplx a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+      const double r = sqrt(creal(a * conj(a)) + creal(b * conj(b)));
+      cs[j] = r > 0.0 ? a / r : 1.0;
+      sn[j] = r > 0.0 ? b / r : 0.0;
+      H[(size_t)j * m + j] = r;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = conj(cs[j]) * g[j];
+      kdim = j + 1;
+      if (iters) (*iters)++;
+      if (cabs(g[j + 1]) <= tol * bnorm) break;
+    }
+    /* back substitution H y = g, then x += V y */
+    for (int i = kdim - 1; i >= 0; i--) {
+      cplx sacc = g[i];
+      for (int t = i + 1; t < kdim; t++) sacc -= H[(size_t)i * m + t] * y[t];
+      y[i] = sacc / H[(size_t)i * m + i];
+    }
+    for (int i = 0; i < kdim; i++) {
+      const cplx *vi = V + (size_t)i * n2;
+      for (size_t k = 0; k < n2; k++) x[k] += y[i] * vi[k];
+    }
+  }
+  free(V); free(w); free(d); free(H); free(cs); free(sn); free(g); free(y);
+  return rc;
+}
+
+int oracle_run_cn(const oracle_params *p, const double *g00, const double *g11,
+                  const double *g22, double dt, long n_steps, double tol, int restart,
+                  int max_restarts, long *iters, cplx *psi) {
+  if (check_params(p) || !psi || n_steps < 0 || !(dt > 0.0) || !(tol > 0.0) || restart < 1 ||
+      restart > 1000 || max_restarts < 0)
+    return -1;
+  const size_t np = (size_t)p->nx * p->ny, n2 = 2 * np;
+  cplx *u = malloc(sizeof(cplx) * 4 * np);
+  cplx *b1 = malloc(sizeof(cplx) * np), *b2 = malloc(sizeof(cplx) * np);
+  cplx *rhs = malloc(sizeof(cplx) * n2), *d = malloc(sizeof(cplx) * n2);
+  if (iters) *iters = 0;
+  int rc = oracle_half_step(p, g00, g11, g22, dt, u);
+  if (rc == 0)
+    rc = oracle_coefficients(p, g00, g11, g22, NULL, NULL, NULL, NULL, NULL, NULL, b1, b2);
+  for (long s = 0; rc == 0 && s < n_steps; s++) {
+    apply_U(p, u, psi);
+    apply_G(p, b1, b2, +1.0, dt, psi, rhs, d);  /* G~ psi */
+    rc = cn_solve(p, b1, b2, dt, rhs, psi, tol, restart, max_restarts, iters);
+    if (rc == 0) apply_U(p, u, psi);
+  }
+  free(u); free(b1); free(b2); free(rhs); free(d);
+  return rc;
+}
+
+/* ---------------------------------------------------------------------------------
  * Observables. norm = hx hy sum |psi|^2 (the discrete l2 norm of Prop. 5.3),
  * norm_gamma = hx hy sum w |psi|^2 (eq. l2gamma with the weight sqrt|g| g^00),
  * density = |psi_1|^2 + |psi_2|^2 (Sec. 6.2), and the energy

@@ -91,6 +91,16 @@ int oracle_run_poly(const oracle_params *p, const double *g00, const double *g11
                     const double *g22, double dt, long n_steps, int family, int order,
                     double complex *psi);
 
+/* n_steps of the Crank-Nicolson scheme (Scheme I, Sec. 5.1 eq. cn): U, then
+ * G psi* = G~ psi with G = I - (dt/2) A, G~ = I + (dt/2) A (A as in oracle_apply_A), then
+ * U. The linear system is solved by restarted GMRES (Sec. 5.1 names Krylov solvers) with
+ * modified Gram-Schmidt in FP64, from psi as initial guess, until the residual is below
+ * tol times |G~ psi|. iters (may be NULL) receives the total Arnoldi steps.
+ * Returns -2 if a solve does not converge within max_restarts cycles of `restart`. */
+int oracle_run_cn(const oracle_params *p, const double *g00, const double *g11,
+                  const double *g22, double dt, long n_steps, double tol, int restart,
+                  int max_restarts, long *iters, double complex *psi);
+
 /* obs = {norm, norm_gamma, energy_re, energy_im}; density may be NULL. */
 int oracle_observables(const oracle_params *p, const double *g00, const double *g11,
                        const double *g22, const double complex *psi, double *obs,

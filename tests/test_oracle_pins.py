@@ -356,6 +356,28 @@ def test_t8_spectral_convergence_in_h(oracle_lib):
 
 
 # --------------------------------------------------------------------------- T9
+def _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
+    """The half-step matrix U as a dense 2N x 2N block-diagonal matrix (scipy's expm,
+    the connection from numpy's FFT derivative)."""
+    npt = nx * ny
+    a1 = c * np.sqrt(g00 / g11)
+    a2 = c * np.sqrt(g00 / g22)
+    me = mass * c * c * np.sqrt(g00)
+    w = np.sqrt(g11 * g22 / g00)
+    omx = 0.5 * np.real(np_deriv(np.log(w * a1), 0, ax))
+    omy = 0.5 * np.real(np_deriv(np.log(w * a2), 1, ay))
+    Ub = np.zeros((2 * npt, 2 * npt), dtype=complex)
+    for j in range(ny):
+        for i in range(nx):
+            k = j * nx + i
+            F = -1j * (a1[j, i] * omx[j, i] * SX + a2[j, i] * omy[j, i] * SY)
+            u = sla.expm(-1j * dt / 2 * (me[j, i] * SZ + F))
+            for r in range(2):
+                for s in range(2):
+                    Ub[r * npt + k, s * npt + k] = u[r, s]
+    return Ub
+
+
 def dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt, symmetric=False):
     """The whole step as a dense 2N x 2N matrix from explicit DFT matrices, the spin
     connection from numpy's FFT derivative and U from scipy's expm."""
@@ -670,3 +692,92 @@ def test_chebyshev_scheme_reaches_the_free_propagator(oracle_lib):
     dt = 0.1  # R = dt 2 pi / h = 2.0: 24 terms are far past convergence
     got = oracle_lib.run_poly(prob, psi0, dt, int(round(T / dt)), oracle_lib.POLY_CHEBYSHEV, 24)
     assert W.rel_l2(got, exact) <= 1e-12
+
+
+# ------------------------------------------------------------ Scheme I (eq. cn)
+@pytest.mark.parametrize("g,mass,c", [((1.0, 1.0, 1.0), 0.0, 1.0), ((1.3, 0.8, 1.1), 0.7, 1.2)])
+def test_cn_per_mode_cayley_closed_form(oracle_lib, g, mass, c):
+    """Constant metric: plane waves are eigenvectors of A, so a step is
+    U (I - dt/2 A(xi))^-1 (I + dt/2 A(xi)) U per mode (a Cayley transform)."""
+    nx, ny, ax, ay = 32, 16, 6.0, 4.0
+    modes = [(1, 0, (1.0, 0.5j)), (3, 14, (0.3 - 0.2j, 0.1)), (31, 5, (0.05, -0.4j)),
+             (16, 8, (0.02, 0.01))]
+    psi0 = W.plane_waves(nx, ny, ax, ay, modes)
+    G = [np.full((ny, nx), v) for v in g]
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=G[0], g11=G[1], g22=G[2])
+    dt, n = 0.05, 40
+    got, _ = oracle_lib.run_cn(prob, psi0, dt, n, tol=1e-15)
+    a1, a2 = c * np.sqrt(g[0] / g[1]), c * np.sqrt(g[0] / g[2])
+    me = mass * c * c * np.sqrt(g[0])
+    U = sla.expm(-1j * dt / 2 * me * SZ)
+    xs, ys = xi_vec(nx, ax), xi_vec(ny, ay)
+    X, Y = W.mesh(nx, ny, ax, ay)
+    ref = np.zeros_like(psi0)
+    for qx, qy, amps in modes:
+        A = -(a1 * 1j * xs[qx] * SX + a2 * 1j * ys[qy] * SY)
+        T = U @ np.linalg.solve(I2 - dt / 2 * A, I2 + dt / 2 * A) @ U
+        v = np.linalg.matrix_power(T, n) @ np.array(amps)
+        e = np.exp(1j * xs[qx] * (X + ax) + 1j * ys[qy] * (Y + ay))
+        ref[0] += v[0] * e
+        ref[1] += v[1] * e
+    assert W.rel_l2(got, ref) <= 1e-12
+
+
+def test_cn_brute_force_dense_solve(oracle_lib):
+    """Tiny curved grid: the step equals U G^-1 G~ U built densely from
+    explicit DFT matrices and numpy's solver."""
+    nx, ny, ax, ay = 8, 4, 3.0, 2.0
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g00 = 1.0 + 0.2 * np.exp(-(X ** 2 + Y ** 2))
+    g11 = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + Y ** 2))
+    g22 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y - 0.3) ** 2))
+    mass, c, dt = 0.7, 1.1, 0.13
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=g00, g11=g11, g22=g22)
+    npt = nx * ny
+    a1 = c * np.sqrt(g00 / g11)
+    a2 = c * np.sqrt(g00 / g22)
+
+    def dmat(n, a):
+        kk = np.arange(n)
+        Fm = np.exp(-2j * np.pi * np.outer(kk, kk) / n)
+        return np.conj(Fm) / n @ np.diag(1j * xi_vec(n, a)) @ Fm
+
+    Dx = np.kron(np.eye(ny), dmat(nx, ax))
+    Dy = np.kron(dmat(ny, ay), np.eye(nx))
+    Z = np.zeros((npt, npt))
+    B1, B2 = np.diag(a1.ravel()), np.diag(a2.ravel())
+    # A = -(b1 sigma_x Dx + b2 sigma_y Dy) on [psi_1; psi_2]
+    A = -(np.block([[Z, B1 @ Dx], [B1 @ Dx, Z]]) +
+          np.block([[Z, -1j * B2 @ Dy], [1j * B2 @ Dy, Z]]))
+    Id = np.eye(2 * npt)
+    Mid = np.linalg.solve(Id - dt / 2 * A, Id + dt / 2 * A)
+    Ub = _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt)
+    ref_step = Ub @ Mid @ Ub
+    for e in range(0, 2 * npt, 5):
+        v = np.zeros(2 * npt, dtype=complex)
+        v[e] = 1.0
+        got, _ = oracle_lib.run_cn(prob, v.reshape(2, ny, nx), dt, 1, tol=1e-15)
+        assert np.abs(got.ravel() - ref_step[:, e]).max() <= 1e-12
+
+
+def test_cn_conserves_the_norm_in_flat_space_and_is_second_order(oracle_lib):
+    """Flat space: G^-1 G~ is a Cayley transform of a skew-Hermitian operator (unitary,
+    Prop. 5.1) and the scheme is second order in time against exp(-i T H(xi))."""
+    n, a, mass, T = 64, 10.0, 0.5, 1.0
+    psi0 = W.wave_packet(n, n, a, a, 1.5, (1.0, -0.5))
+    psi0[1] = 0.5j * psi0[0]
+    prob = problem(oracle_lib, n, n, a, a, mass=mass)
+    got, _ = oracle_lib.run_cn(prob, psi0, 0.05, 20, tol=1e-15)
+    assert abs(np.linalg.norm(got) / np.linalg.norm(psi0) - 1.0) <= 1e-12
+    xs = xi_vec(n, a)
+    KX, KY = np.meshgrid(xs, xs, indexing="xy")
+    E = np.sqrt(KX ** 2 + KY ** 2 + mass ** 2)
+    h0, h1 = np.fft.fft2(psi0[0]), np.fft.fft2(psi0[1])
+    cs, sn = np.cos(T * E), np.sin(T * E) / E
+    r0 = cs * h0 - 1j * sn * (mass * h0 + (KX - 1j * KY) * h1)
+    r1 = cs * h1 - 1j * sn * ((KX + 1j * KY) * h0 - mass * h1)
+    exact = np.stack([np.fft.ifft2(r0), np.fft.ifft2(r1)])
+    errs = [W.rel_l2(oracle_lib.run_cn(prob, psi0, dt, int(round(T / dt)), tol=1e-14)[0], exact)
+            for dt in (0.04, 0.02, 0.01)]
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(o - 2.0) <= 0.15 for o in orders), (errs, orders)
