@@ -50,7 +50,8 @@ typedef enum {
   DIRAC_ECUDA = 4,        /* a CUDA runtime call failed                                   */
   DIRAC_ETIMEOUT = 5,     /* a bounded device wait ran out                                */
   DIRAC_ENONFINITE = 6,   /* the state holds NaN or Inf                                   */
-  DIRAC_ESTATE = 7        /* call out of order (e.g. step before set_state)               */
+  DIRAC_ESTATE = 7,       /* call out of order (e.g. step before set_state)               */
+  DIRAC_ENOCONV = 8       /* Scheme I: the Krylov solver did not reach its tolerance      */
 } dirac_status;
 
 typedef enum { DIRAC_C64 = 0, DIRAC_C128 = 1 } dirac_precision;
@@ -71,7 +72,13 @@ typedef enum {
    * (Sec. 5: Taylor is usually unstable); the degree is set by dirac_set_poly_degree.
    * Each term costs two derivative passes, a transpose and a pointwise combine. */
   DIRAC_SCHEME_POLY_TAYLOR = 2,
-  DIRAC_SCHEME_POLY_CHEBYSHEV = 3
+  DIRAC_SCHEME_POLY_CHEBYSHEV = 3,
+  /* Scheme I (Sec. 5.1 eq. cn): U, then G psi* = G~ psi with G = I + dt/2 alpha.[[grad]]
+   * = I - dt/2 A and G~ = I + dt/2 A (A as above), then U. The linear system is solved by
+   * restarted GMRES (Sec. 5.1: "a Krylov iteration solver") from psi, with FP64 inner
+   * products and Hessenberg arithmetic; see dirac_set_krylov. Unconditionally stable in
+   * flat space (a Cayley transform, Prop. 5.1), second order in time there. */
+  DIRAC_SCHEME_CRANK_NICOLSON = 4
 } dirac_scheme;
 
 /* Spin connection Omega_j (Sec. 2.2). COVARIANT: Omega_j = 1/2 d_j ln(w a^j) with
@@ -167,6 +174,16 @@ dirac_status dirac_set_scheme(dirac_ctx *ctx, int scheme);
  * schemes use three more state-sized device arrays, allocated on the next dirac_step.
  * DIRAC_EINVAL for other values. */
 dirac_status dirac_set_poly_degree(dirac_ctx *ctx, int degree);
+
+/* Krylov solver of Scheme I: relative residual tolerance tol (|G~ psi - G psi*| <= tol
+ * |G~ psi|; 0 = default: 1e-14 for complex128, 3e-7 for complex64), Krylov dimension
+ * `restart` (1..100, default 20; restart + 1 state-sized device arrays, allocated on the
+ * next dirac_step) and at most max_restarts restarts per step (default 100). A step whose
+ * solve does not converge returns DIRAC_ENOCONV and leaves the state invalid. */
+dirac_status dirac_set_krylov(dirac_ctx *ctx, double tol, int restart, int max_restarts);
+
+/* Total Arnoldi steps of Scheme I on this context since its creation. */
+long dirac_krylov_iterations(const dirac_ctx *ctx);
 
 /* CTA shape of the two fused passes (each pass: FFT along a line, k-space multiply,
  * inverse FFT, combine, transposed store): about 256 or 512 threads per CTA for that

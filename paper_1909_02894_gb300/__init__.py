@@ -18,12 +18,15 @@ LIB_PATH = os.path.join(HERE, "libdirac.so")
 
 DIRAC_OK, DIRAC_EINVAL, DIRAC_ENOMEM, DIRAC_EUNSUPPORTED = 0, 1, 2, 3
 DIRAC_ECUDA, DIRAC_ETIMEOUT, DIRAC_ENONFINITE, DIRAC_ESTATE = 4, 5, 6, 7
+DIRAC_ENOCONV = 8
 STATUS_NAMES = {0: "DIRAC_OK", 1: "DIRAC_EINVAL", 2: "DIRAC_ENOMEM", 3: "DIRAC_EUNSUPPORTED",
-                4: "DIRAC_ECUDA", 5: "DIRAC_ETIMEOUT", 6: "DIRAC_ENONFINITE", 7: "DIRAC_ESTATE"}
+                4: "DIRAC_ECUDA", 5: "DIRAC_ETIMEOUT", 6: "DIRAC_ENONFINITE", 7: "DIRAC_ESTATE",
+                8: "DIRAC_ENOCONV"}
 DIRAC_C64, DIRAC_C128 = 0, 1
 DIRAC_CONN_COVARIANT, DIRAC_CONN_PAPER_2D, DIRAC_CONN_NONE = 0, 1, 2
 DIRAC_SCHEME_II, DIRAC_SCHEME_II_SYMMETRIC = 0, 1
 DIRAC_SCHEME_POLY_TAYLOR, DIRAC_SCHEME_POLY_CHEBYSHEV = 2, 3
+DIRAC_SCHEME_CRANK_NICOLSON = 4
 
 # Every symbol the header declares; the CPU tests check that the library exports them.
 ABI_SYMBOLS = (
@@ -31,7 +34,7 @@ ABI_SYMBOLS = (
     "dirac_observables", "dirac_synchronize", "dirac_last_error", "dirac_destroy",
     "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc", "dirac_footprint_bytes",
     "dirac_autotune", "dirac_test_timeout_next_step", "dirac_set_scheme",
-    "dirac_set_poly_degree",
+    "dirac_set_poly_degree", "dirac_set_krylov", "dirac_krylov_iterations",
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
@@ -100,6 +103,9 @@ def lib():
         L.dirac_set_launch.argtypes = [vp, i, i]
         L.dirac_set_scheme.argtypes = [vp, i]
         L.dirac_set_poly_degree.argtypes = [vp, i]
+        L.dirac_set_krylov.argtypes = [vp, d, i, i]
+        L.dirac_krylov_iterations.argtypes = [vp]
+        L.dirac_krylov_iterations.restype = l
         L.dirac_launch_count.argtypes = [vp]
         L.dirac_launch_count.restype = l
         L.dirac_norms_noalloc.argtypes = [vp, vp, i, i, d, d, vp, vp]
@@ -227,6 +233,14 @@ def dirac_set_scheme(ctx, scheme: int):
 
 def dirac_set_poly_degree(ctx, degree: int):
     _check(lib().dirac_set_poly_degree(ctx, int(degree)), ctx)
+
+
+def dirac_set_krylov(ctx, tol: float = 0.0, restart: int = 20, max_restarts: int = 100):
+    _check(lib().dirac_set_krylov(ctx, float(tol), int(restart), int(max_restarts)), ctx)
+
+
+def dirac_krylov_iterations(ctx) -> int:
+    return int(lib().dirac_krylov_iterations(ctx))
 
 
 def dirac_launch_count(ctx) -> int:

@@ -36,6 +36,15 @@ struct dirac_ctx {
   int poly_degree = 8;
   void* pool[3] = {nullptr, nullptr, nullptr};  // polynomial schemes: term buffers
   double bmax[2] = {-1.0, -1.0};                // max |b1|, |b2| (Chebyshev bound)
+  // Scheme I: Krylov solver settings and buffers
+  double krylov_tol = 0.0;  // 0 = precision default
+  int krylov_m = 20, krylov_restarts = 100;
+  long krylov_iters = 0;
+  std::vector<void*> kv;            // basis V_0 .. V_m (state-sized)
+  void* k_rhs = nullptr;            // G~ psi
+  void** k_vptr = nullptr;          // device copy of the basis pointers
+  double* k_partials = nullptr;     // inner-product partial sums
+  double* k_coef = nullptr;         // combination coefficients (device)
   void *mult_xh = nullptr, *u2_n = nullptr;  // symmetric order: x multipliers at dt/2,
                                              // U^2 in the normal layout
   int* d_err = nullptr;       // device error flag written by bounded waits

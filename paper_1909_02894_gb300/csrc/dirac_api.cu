@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -282,6 +283,168 @@ static dirac_status step_poly(dirac_ctx* ctx, long n, double dt) {
   return DIRAC_OK;
 }
 
+// ---- Scheme I (eq. cn): U, G psi* = G~ psi by restarted GMRES, U (U^2 between steps).
+// G v = v - dt/2 A v = v + dt/2 S(v), G~ v = v - dt/2 S(v) (S as in unsplit_apply).
+constexpr int kKrylovBlocks = 304;
+
+// <V_i, w> for i < count, V = the device pointer array starting at slot first.
+template <typename T>
+static dirac_status krylov_dots(dirac_ctx* ctx, int first, int count, const void* w,
+                                std::vector<std::complex<double>>& out) {
+  cudaStream_t st = ctx->stream;
+  CK(launch_multi_dot<T>((const Q4<T>* const*)(ctx->k_vptr + first), count, (const Q4<T>*)w,
+                         npts(ctx), ctx->k_partials, kKrylovBlocks, st),
+     "inner products");
+  std::vector<double> h(2 * (size_t)kKrylovBlocks * count);
+  CK(cudaMemcpyAsync(h.data(), ctx->k_partials, h.size() * sizeof(double),
+                     cudaMemcpyDeviceToHost, st),
+     "inner products");
+  CK(cudaStreamSynchronize(st), "inner products");
+  out.assign(count, 0.0);
+  for (int i = 0; i < count; ++i) {
+    double re = 0.0, im = 0.0;
+    for (int b = 0; b < kKrylovBlocks; ++b) {
+      re += h[2 * ((size_t)i * kKrylovBlocks + b)];
+      im += h[2 * ((size_t)i * kKrylovBlocks + b) + 1];
+    }
+    out[i] = {re, im};
+  }
+  ctx->launches += 1;
+  return DIRAC_OK;
+}
+
+// out += sum_i c_i V_{first + i}
+template <typename T>
+static dirac_status krylov_combine(dirac_ctx* ctx, void* out, int first,
+                                   const std::vector<std::complex<double>>& c) {
+  std::vector<double> h(2 * c.size());
+  for (size_t i = 0; i < c.size(); ++i) {
+    h[2 * i] = c[i].real();
+    h[2 * i + 1] = c[i].imag();
+  }
+  CK(cudaMemcpyAsync(ctx->k_coef, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     ctx->stream),
+     "coefficients");
+  CK(launch_multi_axpy<T>((Q4<T>*)out, (const Q4<T>* const*)(ctx->k_vptr + first), ctx->k_coef,
+                          (int)c.size(), npts(ctx), ctx->stream),
+     "combination");
+  ctx->launches += 1;
+  return DIRAC_OK;
+}
+
+template <typename T>
+static dirac_status step_cn(dirac_ctx* ctx, long n, double dt) {
+  cudaStream_t st = ctx->stream;
+  const size_t np = npts(ctx), bytes = np * sizeof(Q4<T>);
+  const int m = ctx->krylov_m;
+  const double tol = ctx->krylov_tol > 0.0 ? ctx->krylov_tol : (sizeof(T) == 8 ? 1e-14 : 3e-7);
+  // buffers: basis V_0..V_m, the right-hand side, the pointer table (basis, then rhs)
+  while ((int)ctx->kv.size() < m + 1) {
+    void* p = nullptr;
+    CK(dalloc(ctx, &p, bytes), "allocate Krylov basis");
+    ctx->kv.push_back(p);
+  }
+  if (!ctx->k_rhs) CK(dalloc(ctx, &ctx->k_rhs, bytes), "allocate Krylov basis");
+  if (!ctx->scratch1) CK(dalloc(ctx, &ctx->scratch1, bytes), "scratch");
+  if (!ctx->scratch2) CK(dalloc(ctx, &ctx->scratch2, bytes), "scratch");
+  if (!ctx->k_partials)
+    CK(dalloc(ctx, (void**)&ctx->k_partials, 2 * (size_t)kKrylovBlocks * 102 * sizeof(double)),
+       "scratch");
+  if (!ctx->k_coef) CK(dalloc(ctx, (void**)&ctx->k_coef, 2 * 102 * sizeof(double)), "scratch");
+  if (!ctx->k_vptr) CK(dalloc(ctx, (void**)&ctx->k_vptr, 102 * sizeof(void*)), "scratch");
+  {
+    std::vector<void*> table(ctx->kv.begin(), ctx->kv.begin() + m + 1);
+    table.push_back(ctx->k_rhs);
+    CK(cudaMemcpy(ctx->k_vptr, table.data(), table.size() * sizeof(void*), cudaMemcpyHostToDevice),
+       "pointer table");
+  }
+  using cd = std::complex<double>;
+  std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h, h2;
+  for (long s = 0; s < n; ++s) {
+    if (!ctx->u_identity && s == 0) {
+      CK(launch_apply_u<T>((Q4<T>*)ctx->psi, (const Q4<T>*)ctx->u_n, np, st), "half step");
+      ctx->launches += 1;
+    }
+    void* x = ctx->psi;
+    CKS(unsplit_apply<T>(ctx, x, ctx->k_rhs, -0.5 * dt, 0.0, x, 1.0, 0.0, 0.0, nullptr));
+    CKS(krylov_dots<T>(ctx, m + 1, 1, ctx->k_rhs, h));
+    const double bnorm = sqrt(h[0].real());
+    bool converged = false;
+    for (int cycle = 0; cycle <= ctx->krylov_restarts && !converged; ++cycle) {
+      // r = rhs - G x into V_0
+      void* v0 = ctx->kv[0];
+      CKS(unsplit_apply<T>(ctx, x, v0, 0.5 * dt, 0.0, x, 1.0, 0.0, 0.0, nullptr));
+      CK(launch_axpby<T>((Q4<T>*)v0, 1.0, (const Q4<T>*)ctx->k_rhs, -1.0, (const Q4<T>*)v0, np, st),
+         "residual");
+      CKS(krylov_dots<T>(ctx, 0, 1, v0, h));
+      const double beta = sqrt(fmax(h[0].real(), 0.0));
+      if (beta <= tol * bnorm || beta == 0.0) {
+        converged = true;
+        break;
+      }
+      if (cycle == ctx->krylov_restarts) break;
+      CK(launch_scale<T>((Q4<T>*)v0, (const Q4<T>*)v0, 1.0 / beta, 0.0, np, st), "normalise");
+      std::fill(g.begin(), g.end(), cd(0.0));
+      g[0] = beta;
+      int kdim = 0;
+      for (int j = 0; j < m; ++j) {
+        void* w = ctx->kv[j + 1];
+        CKS(unsplit_apply<T>(ctx, ctx->kv[j], w, 0.5 * dt, 0.0, ctx->kv[j], 1.0, 0.0, 0.0,
+                             nullptr));
+        // classical Gram-Schmidt, twice
+        CKS(krylov_dots<T>(ctx, 0, j + 1, w, h));
+        std::vector<cd> neg(j + 1);
+        for (int i = 0; i <= j; ++i) neg[i] = -h[i];
+        CKS(krylov_combine<T>(ctx, w, 0, neg));
+        CKS(krylov_dots<T>(ctx, 0, j + 1, w, h2));
+        for (int i = 0; i <= j; ++i) {
+          neg[i] = -h2[i];
+          h[i] += h2[i];
+        }
+        CKS(krylov_combine<T>(ctx, w, 0, neg));
+        std::vector<cd> nn;
+        CKS(krylov_dots<T>(ctx, j + 1, 1, w, nn));
+        const double hn = sqrt(fmax(nn[0].real(), 0.0));
+        if (hn > 0.0)
+          CK(launch_scale<T>((Q4<T>*)w, (const Q4<T>*)w, 1.0 / hn, 0.0, np, st), "normalise");
+        for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = h[i];
+        H[(size_t)(j + 1) * m + j] = hn;
+        for (int i = 0; i < j; ++i) {  // earlier Givens rotations on column j
+          const cd a = H[(size_t)i * m + j], b = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * b;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b;
+        }
+        const cd a = H[(size_t)j * m + j], b = H[(size_t)(j + 1) * m + j];
+        const double r = sqrt(std::norm(a) + std::norm(b));
+        cs[j] = r > 0.0 ? a / r : cd(1.0);
+        sn[j] = r > 0.0 ? b / r : cd(0.0);
+        H[(size_t)j * m + j] = r;
+        H[(size_t)(j + 1) * m + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = std::conj(cs[j]) * g[j];
+        kdim = j + 1;
+        ctx->krylov_iters += 1;
+        if (std::abs(g[j + 1]) <= tol * bnorm || hn == 0.0) break;
+      }
+      for (int i = kdim - 1; i >= 0; --i) {  // H y = g, then x += V y
+        cd acc = g[i];
+        for (int t = i + 1; t < kdim; ++t) acc -= H[(size_t)i * m + t] * y[t];
+        y[i] = acc / H[(size_t)i * m + i];
+      }
+      CKS(krylov_combine<T>(ctx, x, 0, std::vector<cd>(y.begin(), y.begin() + kdim)));
+      ctx->launches += 3;
+    }
+    if (!converged) return fail(ctx, DIRAC_ENOCONV, "Scheme I: GMRES did not converge");
+    if (!ctx->u_identity) {
+      CK(launch_apply_u<T>((Q4<T>*)ctx->psi, (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n),
+                           np, st),
+         "half step");
+      ctx->launches += 1;
+    }
+  }
+  return DIRAC_OK;
+}
+
 template <typename T>
 static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   if (dt != ctx->dt_cached) {
@@ -291,6 +454,7 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   if (ctx->scheme == DIRAC_SCHEME_II_SYMMETRIC) return step_symmetric<T>(ctx, n);
   if (ctx->scheme == DIRAC_SCHEME_POLY_TAYLOR || ctx->scheme == DIRAC_SCHEME_POLY_CHEBYSHEV)
     return step_poly<T>(ctx, n, dt);
+  if (ctx->scheme == DIRAC_SCHEME_CRANK_NICOLSON) return step_cn<T>(ctx, n, dt);
   LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
   ax.in = (const Q4<T>*)ctx->psi;
   ax.out = (Q4<T>*)ctx->psiT;
@@ -735,7 +899,7 @@ void dirac_destroy(dirac_ctx* ctx) {
 
 dirac_status dirac_set_scheme(dirac_ctx* ctx, int scheme) {
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
-  if (scheme < DIRAC_SCHEME_II || scheme > DIRAC_SCHEME_POLY_CHEBYSHEV)
+  if (scheme < DIRAC_SCHEME_II || scheme > DIRAC_SCHEME_CRANK_NICOLSON)
     return fail(ctx, DIRAC_EINVAL, "unknown scheme");
   if (scheme != ctx->scheme) {
     ctx->scheme = scheme;
@@ -750,6 +914,18 @@ dirac_status dirac_set_poly_degree(dirac_ctx* ctx, int degree) {
   ctx->poly_degree = degree;
   return DIRAC_OK;
 }
+
+dirac_status dirac_set_krylov(dirac_ctx* ctx, double tol, int restart, int max_restarts) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  if (!(tol >= 0.0) || !isfinite(tol) || restart < 1 || restart > 100 || max_restarts < 0)
+    return fail(ctx, DIRAC_EINVAL, "tol >= 0, restart in 1..100, max_restarts >= 0");
+  ctx->krylov_tol = tol;
+  ctx->krylov_m = restart;
+  ctx->krylov_restarts = max_restarts;
+  return DIRAC_OK;
+}
+
+long dirac_krylov_iterations(const dirac_ctx* ctx) { return ctx ? ctx->krylov_iters : 0; }
 
 dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_pass) {
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");

@@ -78,6 +78,20 @@ cudaError_t launch_scale(Q4<T>* out, const Q4<T>* in, double cr, double ci, size
 cudaError_t launch_max_b(const double* a1, const double* a2, const double* sxinv,
                          const double* syinv, int nx, int ny, double* partials,
                          int n_blocks, cudaStream_t st);
+// Krylov building blocks (Scheme I). Partial inner products <V_i, w> (i < count) in
+// FP64: partials[2 (i n_blocks + b)] (re, im) per block b; V is a device array of count
+// pointers.
+template <typename T>
+cudaError_t launch_multi_dot(const Q4<T>* const* V, int count, const Q4<T>* w, size_t n,
+                             double* partials, int n_blocks, cudaStream_t st);
+// out += sum_i coef_i V_i with complex FP64 coef (device array of 2 count doubles).
+template <typename T>
+cudaError_t launch_multi_axpy(Q4<T>* out, const Q4<T>* const* V, const double* coef, int count,
+                              size_t n, cudaStream_t st);
+// out = a x + b y.
+template <typename T>
+cudaError_t launch_axpby(Q4<T>* out, double a, const Q4<T>* x, double b, const Q4<T>* y,
+                         size_t n, cudaStream_t st);
 // J_0(x) .. J_n(x) into out[0..n] (host, FP64); false for x < 0 or n < 0.
 bool bessel_j_series(double x, int n, double* out);
 

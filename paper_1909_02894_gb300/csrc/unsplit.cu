@@ -92,6 +92,85 @@ __global__ void k_max_b(const double* a1, const double* a2, const double* sxinv,
   }
 }
 
+// ---- Krylov building blocks (Scheme I): FP64 accumulation of complex inner products
+// <V_i, w> = sum conj(V_i) w over both components; block (x, i) writes its partial sum
+// of vector i to partials[2 (i gridDim.x + x)], fixed grid so the sum order is fixed.
+template <typename T>
+__global__ void k_multi_dot(const Q4<T>* const* V, const Q4<T>* w, size_t n, double* partials) {
+  __shared__ double sr[TPB], si[TPB];
+  const Q4<T>* v = V[blockIdx.y];
+  double ar = 0.0, ai = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (size_t)gridDim.x * blockDim.x) {
+    const Q4<T> a = v[k], b = w[k];
+    ar += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+    ai += (double)a.x * b.y - (double)a.y * b.x + (double)a.z * b.w - (double)a.w * b.z;
+  }
+  sr[threadIdx.x] = ar;
+  si[threadIdx.x] = ai;
+  __syncthreads();
+  for (int s = TPB / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      sr[threadIdx.x] += sr[threadIdx.x + s];
+      si[threadIdx.x] += si[threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const size_t o = 2 * ((size_t)blockIdx.y * gridDim.x + blockIdx.x);
+    partials[o] = sr[0];
+    partials[o + 1] = si[0];
+  }
+}
+
+// out += sum_i c_i V_i (c complex, coef[2 i], coef[2 i + 1]; FP64 coefficients)
+template <typename T>
+__global__ void k_multi_axpy(Q4<T>* out, const Q4<T>* const* V, const double* coef, int count,
+                             size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  Q4<T> o = out[k];
+  for (int i = 0; i < count; ++i) {
+    const T cr = (T)coef[2 * i], ci = (T)coef[2 * i + 1];
+    const Q4<T> v = V[i][k];
+    o.x += cr * v.x - ci * v.y;
+    o.y += cr * v.y + ci * v.x;
+    o.z += cr * v.z - ci * v.w;
+    o.w += cr * v.w + ci * v.z;
+  }
+  out[k] = o;
+}
+
+// out = a x + b y (real a, b)
+template <typename T>
+__global__ void k_axpby(Q4<T>* out, T a, const Q4<T>* x, T b, const Q4<T>* y, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const Q4<T> p = x[k], q = y[k];
+  out[k] = {a * p.x + b * q.x, a * p.y + b * q.y, a * p.z + b * q.z, a * p.w + b * q.w};
+}
+
+template <typename T>
+cudaError_t launch_multi_dot(const Q4<T>* const* V, int count, const Q4<T>* w, size_t n,
+                             double* partials, int n_blocks, cudaStream_t st) {
+  k_multi_dot<T><<<dim3(n_blocks, count), TPB, 0, st>>>(V, w, n, partials);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_multi_axpy(Q4<T>* out, const Q4<T>* const* V, const double* coef, int count,
+                              size_t n, cudaStream_t st) {
+  k_multi_axpy<T><<<blocks_for(n), TPB, 0, st>>>(out, V, coef, count, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_axpby(Q4<T>* out, double a, const Q4<T>* x, double b, const Q4<T>* y,
+                         size_t n, cudaStream_t st) {
+  k_axpby<T><<<blocks_for(n), TPB, 0, st>>>(out, (T)a, x, (T)b, y, n);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n, cudaStream_t st) {
   k_apply_u<T><<<blocks_for(n), TPB, 0, st>>>(psi, u, n);
@@ -163,7 +242,13 @@ bool bessel_j_series(double x, int n, double* out) {
       int, int, double, double, const Q4<T>*, double, double, double, Q4<T>*, Q4<T>*,       \
       cudaStream_t);                                                                         \
   template cudaError_t launch_scale<T>(Q4<T>*, const Q4<T>*, double, double, size_t,         \
-                                       cudaStream_t);
+                                       cudaStream_t);                                        \
+  template cudaError_t launch_multi_dot<T>(const Q4<T>* const*, int, const Q4<T>*, size_t,    \
+                                           double*, int, cudaStream_t);                      \
+  template cudaError_t launch_multi_axpy<T>(Q4<T>*, const Q4<T>* const*, const double*, int,  \
+                                            size_t, cudaStream_t);                           \
+  template cudaError_t launch_axpby<T>(Q4<T>*, double, const Q4<T>*, double, const Q4<T>*,   \
+                                       size_t, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST
