@@ -207,6 +207,8 @@ def cpu_baseline(w, scheme="printed", degree=8):
     prob = oracle.Problem.from_workload(w)
 
     def run(n):
+        if scheme == "cn":
+            return oracle.run_cn(prob, w.psi0, w.dt, n, tol=1e-14)[0]
         if scheme in ("taylor", "chebyshev"):
             fam = oracle.POLY_TAYLOR if scheme == "taylor" else oracle.POLY_CHEBYSHEV
             return oracle.run_poly(prob, w.psi0, w.dt, n, fam, degree)
@@ -375,9 +377,10 @@ def main():
     ap.add_argument("--sustainable-rate", type=float, default=4.0)
     ap.add_argument("--sustainable-seconds", type=float, default=20.0)
     ap.add_argument("--scheme", default="printed",
-                    choices=["printed", "symmetric", "taylor", "chebyshev"],
-                    help="Scheme II (printed x, y or symmetric x/2, y, x/2 order) or the "
-                         "polynomial scheme with a Taylor or Chebyshev middle step")
+                    choices=["printed", "symmetric", "taylor", "chebyshev", "cn"],
+                    help="Scheme II (printed x, y or symmetric x/2, y, x/2 order), the "
+                         "polynomial scheme with a Taylor or Chebyshev middle step, or "
+                         "Scheme I (Crank-Nicolson, GMRES)")
     ap.add_argument("--poly-degree", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -401,10 +404,12 @@ def main():
     prec = D.DIRAC_C64 if prec_name == "c64" else D.DIRAC_C128
     symmetric = args.scheme == "symmetric"
     poly = args.scheme in ("taylor", "chebyshev")
+    cn = args.scheme == "cn"
     passes = 3 if symmetric else 2
     scheme_id = {"printed": D.DIRAC_SCHEME_II, "symmetric": D.DIRAC_SCHEME_II_SYMMETRIC,
                  "taylor": D.DIRAC_SCHEME_POLY_TAYLOR,
-                 "chebyshev": D.DIRAC_SCHEME_POLY_CHEBYSHEV}[args.scheme]
+                 "chebyshev": D.DIRAC_SCHEME_POLY_CHEBYSHEV,
+                 "cn": D.DIRAC_SCHEME_CRANK_NICOLSON}[args.scheme]
     if symmetric:
         # three sweeps of psi, b - 1 read in each, U^2 once: 124 B (complex64)
         bytes_pt = bytes_pt // 88 * 124
@@ -433,6 +438,7 @@ def main():
 
     # ---- device-resident timed region
     l0 = D.dirac_launch_count(sim.ctx)
+    it0 = D.dirac_krylov_iterations(sim.ctx)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
@@ -458,7 +464,16 @@ def main():
     achieved = alg_bytes_launch / per_launch_s / 1e9
     if poly:  # many kernels per step: the whole step against the roofline
         achieved = bytes_pt * pts / (ms * 1e-3 / args.steps) / 1e9
-    traffic = None if (symmetric or poly) else ncu_traffic(args.workload)
+    krylov = None
+    if cn:  # bytes of the operator applications and Krylov vector work actually done
+        s_ = bytes_pt // 88 * 16
+        iters = D.dirac_krylov_iterations(sim.ctx) - it0
+        apply_b = 6 * s_ + 2 * s_ + 16 + 2 * s_  # passes, combine (dx, dy, a, prev, out)
+        per_iter = apply_b + 4 * 3 * s_ + 2 * s_  # G v, two Gram-Schmidt sweeps, norm
+        bytes_pt = (iters * per_iter + args.steps * (3 * apply_b + 2 * s_ + 16)) / args.steps
+        achieved = bytes_pt * pts / (ms * 1e-3 / args.steps) / 1e9
+        krylov = {"arnoldi_steps_per_step": iters / args.steps}
+    traffic = None if (symmetric or poly or cn) else ncu_traffic(args.workload)
 
     # ---- end to end through the public API with pinned host buffers
     e2e = None
@@ -491,6 +506,7 @@ def main():
                                   "symmetric": "Scheme II, symmetric x/2-y-x/2",
                                   "taylor": f"polynomial, Taylor degree {args.poly_degree}",
                                   "chebyshev": f"polynomial, Chebyshev degree {args.poly_degree}",
+                                  "cn": "Scheme I (Crank-Nicolson, restarted GMRES)",
                                   }[args.scheme],
                        "dt": w.dt, "absorber": w.pml_width_x, "parallelism": "replicas",
                        "l2": "inputs larger than L2 (no flush)"
@@ -499,12 +515,14 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_kind,
                          "kernel": "whole step (derivative passes, transposes, combines)"
-                         if poly else kernel_name(w, prec_name),
+                         if (poly or cn) else kernel_name(w, prec_name),
                          "algorithmic_bytes_per_point_step": bytes_pt},
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
             "e2e": e2e,
         }
+        if krylov:
+            line["krylov"] = krylov
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w, scheme=args.scheme,
                                                 degree=args.poly_degree)
