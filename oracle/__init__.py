@@ -44,6 +44,7 @@ class _Params(C.Structure):
         ("conn", C.c_int),
         ("pml_wx", C.c_int), ("pml_wy", C.c_int), ("pml_type", C.c_int),
         ("sigma0", C.c_double), ("theta", C.c_double),
+        ("V", C.c_void_p), ("Ax", C.c_void_p), ("Ay", C.c_void_p),
     ]
 
 
@@ -115,17 +116,26 @@ class Problem:
     g00: np.ndarray = None
     g11: np.ndarray = None
     g22: np.ndarray = None
+    V: np.ndarray = None   # static potentials (None = 0), see oracle_params
+    Ax: np.ndarray = None
+    Ay: np.ndarray = None
 
     @classmethod
     def from_workload(cls, w, conn=None):
         return cls(nx=w.nx, ny=w.ny, ax=w.ax, ay=w.ay, mass=w.mass, c=w.c,
                    conn=w.conn if conn is None else conn, pml_wx=w.pml_width_x,
                    pml_wy=w.pml_width_y, pml_type=w.pml_type, sigma0=w.sigma0,
-                   theta=w.theta, g00=w.g00, g11=w.g11, g22=w.g22)
+                   theta=w.theta, g00=w.g00, g11=w.g11, g22=w.g22,
+                   V=getattr(w, "V", None), Ax=getattr(w, "Ax", None), Ay=getattr(w, "Ay", None))
 
     def _params(self):
+        s = (self.ny, self.nx)
+        # the arrays must outlive the call that receives the struct: keep them here
+        self._pot = [None if f is None else np.ascontiguousarray(f, dtype=np.float64).reshape(s)
+                     for f in (self.V, self.Ax, self.Ay)]
+        ptrs = [None if f is None else f.ctypes.data for f in self._pot]
         return _Params(self.nx, self.ny, self.ax, self.ay, self.mass, self.c, self.conn,
-                       self.pml_wx, self.pml_wy, self.pml_type, self.sigma0, self.theta)
+                       self.pml_wx, self.pml_wy, self.pml_type, self.sigma0, self.theta, *ptrs)
 
     def _g(self):
         s = (self.ny, self.nx)

@@ -280,10 +280,19 @@ int oracle_half_step(const oracle_params *p, const double *g00, const double *g1
   int rc = oracle_coefficients(p, g00, g11, g22, a1, a2, me, NULL, ox, oy, NULL, NULL);
   if (rc == 0) {
     for (size_t k = 0; k < np; k++) {
+      /* exponent -i dt/2 [meff sigma_z + F], F = -i sum_j a^j Omega_j sigma_j
+       *   - sum_j a^j A_j sigma_j + V I  (the potentials: a scalar phase and an imaginary
+       *   part of v_1, v_2) */
       cplx v1 = -0.5 * dt * a1[k] * ox[k];
       cplx v2 = -0.5 * dt * a2[k] * oy[k];
       cplx v3 = -0.5 * I * dt * me[k];
+      if (p->Ax) v1 += 0.5 * I * dt * a1[k] * p->Ax[k];
+      if (p->Ay) v2 += 0.5 * I * dt * a2[k] * p->Ay[k];
       exp_pauli(v1, v2, v3, &u[4 * k]);
+      if (p->V) {
+        const cplx ph = cexp(-0.5 * I * dt * p->V[k]);
+        for (int t = 0; t < 4; t++) u[4 * k + t] *= ph;
+      }
     }
   }
   free(a1); free(a2); free(me); free(ox); free(oy);

@@ -36,6 +36,11 @@ typedef struct {
   int pml_wx, pml_wy;  /* absorbing-layer width in grid points per side, 0 = none        */
   int pml_type;        /* 1..6 = the paper's types I..VI (Sec. 3)                        */
   double sigma0, theta;
+  /* static electromagnetic potentials (Sec. 2, the F of the curved-space Hamiltonian):
+   * [ny][nx] fields, NULL = 0. V is the scalar potential energy, entering H as + V I;
+   * Ax, Ay are the vector potential times the charge, entering H as
+   * - sum_j a^j A_j sigma_j (from alpha.(-i grad - e A)). They act through U only. */
+  const double *V, *Ax, *Ay;
 } oracle_params;
 
 /* Forward DFT psi~_p = sum_k psi_k exp(-2 pi i p k / n), inverse with 1/n (Sec. 5). */

@@ -356,9 +356,10 @@ def test_t8_spectral_convergence_in_h(oracle_lib):
 
 
 # --------------------------------------------------------------------------- T9
-def _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
+def _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt, V=None, Ax=None, Ay=None):
     """The half-step matrix U as a dense 2N x 2N block-diagonal matrix (scipy's expm,
-    the connection from numpy's FFT derivative)."""
+    the connection from numpy's FFT derivative; potentials: F gains
+    -(a1 Ax sigma_x + a2 Ay sigma_y) + V)."""
     npt = nx * ny
     a1 = c * np.sqrt(g00 / g11)
     a2 = c * np.sqrt(g00 / g22)
@@ -371,6 +372,12 @@ def _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt):
         for i in range(nx):
             k = j * nx + i
             F = -1j * (a1[j, i] * omx[j, i] * SX + a2[j, i] * omy[j, i] * SY)
+            if Ax is not None:
+                F = F - a1[j, i] * Ax[j, i] * SX
+            if Ay is not None:
+                F = F - a2[j, i] * Ay[j, i] * SY
+            if V is not None:
+                F = F + V[j, i] * I2
             u = sla.expm(-1j * dt / 2 * (me[j, i] * SZ + F))
             for r in range(2):
                 for s in range(2):
@@ -781,3 +788,72 @@ def test_cn_conserves_the_norm_in_flat_space_and_is_second_order(oracle_lib):
             for dt in (0.04, 0.02, 0.01)]
     orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(abs(o - 2.0) <= 0.15 for o in orders), (errs, orders)
+
+
+# ------------------------------------------------- static potentials (Sec. 2, F)
+def test_constant_scalar_potential_is_a_global_phase(oracle_lib):
+    """V I commutes with every sub-step: a constant V multiplies the V = 0 result by
+    exp(-i V n dt) (H gains + V I)."""
+    w = W.plain_128(n=64, steps=30)
+    prob0 = oracle_lib.Problem.from_workload(w)
+    ref = oracle_lib.run(prob0, w.psi0, w.dt, 30)
+    prob = oracle_lib.Problem.from_workload(w)
+    prob.V = np.full((w.ny, w.nx), 0.8)
+    got = oracle_lib.run(prob, w.psi0, w.dt, 30)
+    assert W.rel_l2(got, np.exp(-1j * 0.8 * 30 * w.dt) * ref) <= 1e-13
+
+
+def test_constant_vector_potential_per_mode_closed_form(oracle_lib):
+    """Constant metric and potentials: plane waves stay plane waves; a step is
+    U_A K(xi) U_A per mode with U_A = expm(-i dt/2 (m sigma_z - a1 Ax sigma_x
+    - a2 Ay sigma_y + V)) from scipy."""
+    nx, ny, ax, ay = 32, 16, 6.0, 4.0
+    g = (1.3, 0.8, 1.1)
+    mass, c, Ax, Ay, V = 0.7, 1.0, 0.4, -0.3, 0.25
+    modes = [(1, 0, (1.0, 0.5j)), (3, 14, (0.3 - 0.2j, 0.1)), (31, 5, (0.05, -0.4j))]
+    psi0 = W.plane_waves(nx, ny, ax, ay, modes)
+    G = [np.full((ny, nx), v) for v in g]
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=G[0], g11=G[1], g22=G[2])
+    prob.V, prob.Ax, prob.Ay = (np.full((ny, nx), v) for v in (V, Ax, Ay))
+    dt, n = 0.03, 60
+    got = oracle_lib.run(prob, psi0, dt, n)
+    a1, a2 = c * np.sqrt(g[0] / g[1]), c * np.sqrt(g[0] / g[2])
+    me = mass * c * c * np.sqrt(g[0])
+    UA = sla.expm(-1j * dt / 2 * (me * SZ - a1 * Ax * SX - a2 * Ay * SY + V * I2))
+    xs, ys = xi_vec(nx, ax), xi_vec(ny, ay)
+    X, Y = W.mesh(nx, ny, ax, ay)
+    ref = np.zeros_like(psi0)
+    for qx, qy, amps in modes:
+        Kx = a1 * sla.expm(-1j * dt * xs[qx] * SX) + (1 - a1) * I2
+        Ky = a2 * sla.expm(-1j * dt * ys[qy] * SY) + (1 - a2) * I2
+        v = np.linalg.matrix_power(UA @ Ky @ Kx @ UA, n) @ np.array(amps)
+        e = np.exp(1j * xs[qx] * (X + ax) + 1j * ys[qy] * (Y + ay))
+        ref[0] += v[0] * e
+        ref[1] += v[1] * e
+    assert W.rel_l2(got, ref) <= 1e-12
+
+
+def test_potentials_brute_force_dense_step(oracle_lib):
+    nx, ny, ax, ay = 8, 4, 3.0, 2.0
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g00 = 1.0 + 0.2 * np.exp(-(X ** 2 + Y ** 2))
+    g11 = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + Y ** 2))
+    g22 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y - 0.3) ** 2))
+    V = 0.5 * np.exp(-X ** 2)
+    Ax = 0.3 * np.cos(np.pi * Y / ay)
+    Ay = -0.2 * X / ax
+    mass, c, dt = 0.7, 1.1, 0.13
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=g00, g11=g11, g22=g22)
+    prob.V, prob.Ax, prob.Ay = V, Ax, Ay
+    M = dense_step(nx, ny, ax, ay, g00, g11, g22, mass, c, dt)
+    U0 = _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt)
+    UA = _dense_u(nx, ny, ax, ay, g00, g11, g22, mass, c, dt, V=V, Ax=Ax, Ay=Ay)
+    # dense_step is U0 S U0; swap in the potentials' U
+    inner = np.linalg.solve(U0, np.linalg.solve(U0.T, M.T).T)
+    ref = UA @ inner @ UA
+    npt = nx * ny
+    for e in range(2 * npt):
+        v = np.zeros(2 * npt, dtype=complex)
+        v[e] = 1.0
+        got = oracle_lib.run(prob, v.reshape(2, ny, nx), dt, 1).ravel()
+        assert np.abs(got - ref[:, e]).max() <= 1e-12
