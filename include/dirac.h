@@ -170,6 +170,18 @@ void dirac_destroy(dirac_ctx *ctx);
  * DIRAC_EUNSUPPORTED). DIRAC_EINVAL for other values. */
 dirac_status dirac_set_scheme(dirac_ctx *ctx, int scheme);
 
+/* Static electromagnetic potentials (Sec. 2: the F of the curved-space Hamiltonian),
+ * host [ny][nx] FP64 arrays copied by the call; NULL means 0 (all NULL removes them).
+ * V is the scalar potential energy, entering H as + V I; Ax, Ay are the vector potential
+ * times the charge, entering H as - sum_j a^j A_j sigma_j (from alpha.(-i grad - e A)).
+ * They act through the half-step matrix U, which becomes a general complex 2x2 matrix per
+ * point, applied by its own pointwise kernel (U before the first pass of a call, U^2
+ * between steps, U after the last) instead of inside the line passes. The energy that
+ * dirac_observables reports does not include the potentials. Contexts with potentials
+ * cannot join a batch. DIRAC_EINVAL for non-finite values. */
+dirac_status dirac_set_potentials(dirac_ctx *ctx, const double *V, const double *Ax,
+                                  const double *Ay);
+
 /* Degree N_p of the polynomial schemes' middle step (1..256; default 8). The polynomial
  * schemes use three more state-sized device arrays, allocated on the next dirac_step.
  * DIRAC_EINVAL for other values. */

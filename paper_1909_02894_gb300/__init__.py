@@ -35,6 +35,7 @@ ABI_SYMBOLS = (
     "dirac_set_launch", "dirac_launch_count", "dirac_norms_noalloc", "dirac_footprint_bytes",
     "dirac_autotune", "dirac_test_timeout_next_step", "dirac_set_scheme",
     "dirac_set_poly_degree", "dirac_set_krylov", "dirac_krylov_iterations",
+    "dirac_set_potentials",
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
@@ -104,6 +105,7 @@ def lib():
         L.dirac_set_scheme.argtypes = [vp, i]
         L.dirac_set_poly_degree.argtypes = [vp, i]
         L.dirac_set_krylov.argtypes = [vp, d, i, i]
+        L.dirac_set_potentials.argtypes = [vp, vp, vp, vp]
         L.dirac_krylov_iterations.argtypes = [vp]
         L.dirac_krylov_iterations.restype = l
         L.dirac_launch_count.argtypes = [vp]
@@ -241,6 +243,17 @@ def dirac_set_krylov(ctx, tol: float = 0.0, restart: int = 20, max_restarts: int
 
 def dirac_krylov_iterations(ctx) -> int:
     return int(lib().dirac_krylov_iterations(ctx))
+
+
+def dirac_set_potentials(ctx, V=None, Ax=None, Ay=None, shape=None):
+    """Static potentials as [ny][nx] arrays (None = 0); the library copies them."""
+    arrs = [None if f is None else np.ascontiguousarray(f, dtype=np.float64) for f in (V, Ax, Ay)]
+    if shape is not None:
+        for a in arrs:
+            if a is not None and a.shape != tuple(shape):
+                raise ValueError(f"potential shape {a.shape} != {tuple(shape)}")
+    ptrs = [None if a is None else a.ctypes.data for a in arrs]
+    _check(lib().dirac_set_potentials(ctx, *ptrs), ctx)
 
 
 def dirac_launch_count(ctx) -> int:

@@ -36,6 +36,11 @@ struct dirac_ctx {
   int poly_degree = 8;
   void* pool[3] = {nullptr, nullptr, nullptr};  // polynomial schemes: term buffers
   double bmax[2] = {-1.0, -1.0};                // max |b1|, |b2| (Chebyshev bound)
+  // static potentials (device FP64 [ny][nx], null = 0) and the general half-step matrices
+  double *pot_v = nullptr, *pot_ax = nullptr, *pot_ay = nullptr;
+  bool pot_use[3] = {false, false, false};  // V, Ax, Ay set
+  bool has_pot = false;
+  void *ug = nullptr, *ug2 = nullptr;  // U and U^2, two Q4 per point
   // Scheme I: Krylov solver settings and buffers
   double krylov_tol = 0.0;  // 0 = precision default
   int krylov_m = 20, krylov_restarts = 100;

@@ -106,6 +106,17 @@ static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
        "half-step matrices");
     ctx->launches += 1;
   }
+  if (ctx->has_pot) {
+    if (!ctx->ug) CK(dalloc(ctx, &ctx->ug, 2 * npts(ctx) * sizeof(Q4<T>)), "allocate half-step");
+    if (!ctx->ug2) CK(dalloc(ctx, &ctx->ug2, 2 * npts(ctx) * sizeof(Q4<T>)), "allocate half-step");
+    CK(launch_halfstep_general<T>(ctx->a1, ctx->a2, ctx->meff, ctx->omx, ctx->omy,
+                                  ctx->pot_use[0] ? ctx->pot_v : nullptr,
+                                  ctx->pot_use[1] ? ctx->pot_ax : nullptr,
+                                  ctx->pot_use[2] ? ctx->pot_ay : nullptr, ctx->nx, ctx->ny, dt,
+                                  (Q4<T>*)ctx->ug, (Q4<T>*)ctx->ug2, st),
+       "half-step matrices with potentials");
+    ctx->launches += 1;
+  }
   CK(launch_step_mult<T>(ctx->nx, ctx->ax, dt, (Q4<T>*)ctx->mult_x, st), "x multipliers");
   CK(launch_step_mult<T>(ctx->ny, ctx->ay, dt, (Q4<T>*)ctx->mult_y, st), "y multipliers");
   ctx->launches += 2;
@@ -115,6 +126,26 @@ static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
     ctx->launches += 1;
   }
   ctx->dt_cached = dt;
+  return DIRAC_OK;
+}
+
+// psi <- U psi (squared = false) or U^2 psi in the normal layout, outside the passes: the
+// general matrices when potentials are set, else the real-form ones (none when U = I).
+template <typename T>
+static dirac_status apply_half(dirac_ctx* ctx, void* psi, bool squared) {
+  const size_t np = npts(ctx);
+  if (ctx->has_pot) {
+    CK(launch_apply_ug<T>((Q4<T>*)psi, (const Q4<T>*)(squared ? ctx->ug2 : ctx->ug), np,
+                          ctx->stream),
+       "half step");
+  } else if (!ctx->u_identity) {
+    CK(launch_apply_u<T>((Q4<T>*)psi, (const Q4<T>*)(squared ? ctx->u2_n : ctx->u_n), np,
+                         ctx->stream),
+       "half step");
+  } else {
+    return DIRAC_OK;
+  }
+  ctx->launches += 1;
   return DIRAC_OK;
 }
 
@@ -135,22 +166,32 @@ static dirac_status step_symmetric(dirac_ctx* ctx, long n) {
   void* oth = ctx->psiT;
   const int opt_x = pass_opt(ctx, ctx->threads_x, ctx->nx);
   const int opt_y = pass_opt(ctx, ctx->threads_y, ctx->ny);
+  const bool fused = !ctx->has_pot;  // potentials: U applied by its own kernel
+  if (!fused) {
+    dirac_status r = apply_half<T>(ctx, cur, false);
+    if (r != DIRAC_OK) return r;
+  }
   for (long s = 0; s < n; ++s) {
     LinePassArgs<T> a1 = ax, a3 = ax;
     a1.in = (const Q4<T>*)cur;
     a1.out = (Q4<T>*)oth;
-    a1.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
+    a1.u_load = (fused && s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
     ay.in = (const Q4<T>*)oth;
     ay.out = (Q4<T>*)cur;
     a3.in = (const Q4<T>*)cur;
     a3.out = (Q4<T>*)oth;
     a3.store_normal = 1;
-    a3.u_store = ctx->u_identity ? nullptr
-                                 : (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n);
+    a3.u_store = (!fused || ctx->u_identity)
+                     ? nullptr
+                     : (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n);
     CK(launch_line_pass<T>(a1, MODE_STEP, opt_x, ctx->stream), "x pass (dt/2)");
     CK(launch_line_pass<T>(ay, MODE_STEP, opt_y, ctx->stream), "y pass");
     CK(launch_line_pass<T>(a3, MODE_STEP, opt_x, ctx->stream), "x pass (dt/2, rows)");
     ctx->launches += 3;
+    if (!fused) {
+      dirac_status r = apply_half<T>(ctx, oth, s + 1 < n);
+      if (r != DIRAC_OK) return r;
+    }
     void* t = cur;
     cur = oth;
     oth = t;
@@ -234,10 +275,7 @@ static dirac_status step_poly(dirac_ctx* ctx, long n, double dt) {
       return fail(ctx, DIRAC_EINVAL, "no Chebyshev bound for this grid and dt");
   }
   for (long s = 0; s < n; ++s) {
-    if (!ctx->u_identity && s == 0) {
-      CK(launch_apply_u<T>((Q4<T>*)ctx->psi, (const Q4<T>*)ctx->u_n, np, st), "half step");
-      ctx->launches += 1;
-    }
+    if (s == 0) CKS(apply_half<T>(ctx, ctx->psi, false));
     void* bufs[4] = {ctx->psi, ctx->pool[0], ctx->pool[1], ctx->pool[2]};
     void* acc = bufs[3];
     if (!cheb) {
@@ -273,12 +311,7 @@ static dirac_status step_poly(dirac_ctx* ctx, long n, double dt) {
     for (void* b : bufs)
       if (b != acc) ctx->pool[k++] = b;
     ctx->psi = acc;
-    if (!ctx->u_identity) {
-      CK(launch_apply_u<T>((Q4<T>*)ctx->psi,
-                           (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n), np, st),
-         "half step");
-      ctx->launches += 1;
-    }
+    CKS(apply_half<T>(ctx, ctx->psi, s + 1 < n));
   }
   return DIRAC_OK;
 }
@@ -361,10 +394,7 @@ static dirac_status step_cn(dirac_ctx* ctx, long n, double dt) {
   using cd = std::complex<double>;
   std::vector<cd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m), h, h2;
   for (long s = 0; s < n; ++s) {
-    if (!ctx->u_identity && s == 0) {
-      CK(launch_apply_u<T>((Q4<T>*)ctx->psi, (const Q4<T>*)ctx->u_n, np, st), "half step");
-      ctx->launches += 1;
-    }
+    if (s == 0) CKS(apply_half<T>(ctx, ctx->psi, false));
     void* x = ctx->psi;
     CKS(unsplit_apply<T>(ctx, x, ctx->k_rhs, -0.5 * dt, 0.0, x, 1.0, 0.0, 0.0, nullptr));
     CKS(krylov_dots<T>(ctx, m + 1, 1, ctx->k_rhs, h));
@@ -435,12 +465,7 @@ static dirac_status step_cn(dirac_ctx* ctx, long n, double dt) {
       ctx->launches += 3;
     }
     if (!converged) return fail(ctx, DIRAC_ENOCONV, "Scheme I: GMRES did not converge");
-    if (!ctx->u_identity) {
-      CK(launch_apply_u<T>((Q4<T>*)ctx->psi, (const Q4<T>*)(s + 1 == n ? ctx->u_n : ctx->u2_n),
-                           np, st),
-         "half step");
-      ctx->launches += 1;
-    }
+    CKS(apply_half<T>(ctx, ctx->psi, s + 1 < n));
   }
   return DIRAC_OK;
 }
@@ -466,17 +491,20 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   ay.beta = (const T*)ctx->beta2T;
   ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
   ctx->test_timeout_next = 0;
+  const bool fused = !ctx->has_pot;  // potentials: U applied by its own kernel
+  if (!fused) CKS(apply_half<T>(ctx, ctx->psi, false));
   for (long s = 0; s < n; ++s) {
-    ax.u_load = (s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
+    ax.u_load = (fused && s == 0 && !ctx->u_identity) ? (const Q4<T>*)ctx->u_n : nullptr;
     ax.u_store = nullptr;
     CK(launch_line_pass<T>(ax, MODE_STEP, pass_opt(ctx, ctx->threads_x, ctx->nx), ctx->stream),
        "x pass");
     ay.u_load = nullptr;
-    ay.u_store = ctx->u_identity ? nullptr
-                                 : (const Q4<T>*)(s + 1 == n ? ctx->u_t : ctx->u2_t);
+    ay.u_store = (!fused || ctx->u_identity) ? nullptr
+                                             : (const Q4<T>*)(s + 1 == n ? ctx->u_t : ctx->u2_t);
     CK(launch_line_pass<T>(ay, MODE_STEP, pass_opt(ctx, ctx->threads_y, ctx->ny), ctx->stream),
        "y pass");
     ctx->launches += 2;
+    if (!fused) CKS(apply_half<T>(ctx, ctx->psi, s + 1 < n));
   }
   return DIRAC_OK;
 }
@@ -905,6 +933,33 @@ dirac_status dirac_set_scheme(dirac_ctx* ctx, int scheme) {
     ctx->scheme = scheme;
     ctx->dt_cached = 0.0;  // the tables of the new order are made on the next step
   }
+  return DIRAC_OK;
+}
+
+dirac_status dirac_set_potentials(dirac_ctx* ctx, const double* V, const double* Ax,
+                                  const double* Ay) {
+  if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
+  const size_t n = npts(ctx);
+  const double* src[3] = {V, Ax, Ay};
+  double** dst[3] = {&ctx->pot_v, &ctx->pot_ax, &ctx->pot_ay};
+  for (int f = 0; f < 3; ++f)
+    if (src[f])
+      for (size_t k = 0; k < n; ++k)
+        if (!isfinite(src[f][k])) return fail(ctx, DIRAC_EINVAL, "potentials must be finite");
+  for (int f = 0; f < 3; ++f) {
+    ctx->pot_use[f] = src[f] != nullptr;
+    if (!src[f]) continue;  // an earlier buffer stays allocated for a later call
+    if (!*dst[f]) {
+      void* p = nullptr;
+      if (dalloc(ctx, &p, n * sizeof(double)) != cudaSuccess)
+        return fail(ctx, DIRAC_ENOMEM, "allocate potentials");
+      *dst[f] = (double*)p;
+    }
+    cudaError_t e = cudaMemcpy(*dst[f], src[f], n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy potentials");
+  }
+  ctx->has_pot = V || Ax || Ay;
+  ctx->dt_cached = 0.0;  // the half-step matrices are made again on the next step
   return DIRAC_OK;
 }
 

@@ -58,6 +58,17 @@ cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream
 template <typename T>
 cudaError_t launch_deriv_mult(int n, double a, Q4<T>* mult, cudaStream_t st);
 
+// Half step with static potentials: general complex U and U^2 per point (normal layout,
+// two Q4 per point holding U - I: (d00, u01), (u10, d11)); V, Ax, Ay may be null (0).
+template <typename T>
+cudaError_t launch_halfstep_general(const double* a1, const double* a2, const double* meff,
+                                    const double* omx, const double* omy, const double* V,
+                                    const double* Ax, const double* Ay, int nx, int ny,
+                                    double dt, Q4<T>* ug, Q4<T>* ug2, cudaStream_t st);
+// psi <- U psi for such a general U.
+template <typename T>
+cudaError_t launch_apply_ug(Q4<T>* psi, const Q4<T>* ug, size_t n, cudaStream_t st);
+
 // ---- unsplit polynomial scheme (unsplit.cu)
 // psi <- U psi at every point (normal layout).
 template <typename T>

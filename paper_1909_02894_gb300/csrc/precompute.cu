@@ -166,6 +166,96 @@ __global__ void k_halfstep(const double* a1, const double* a2, const double* mef
   if (u2_n) u2_n[k] = U2;
 }
 
+// ---- half step with static potentials: a general complex 2x2 matrix per point
+struct Z {  // FP64 complex for the per-point exponential
+  double r, i;
+};
+__device__ inline Z zmul(Z a, Z b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ inline Z zadd(Z a, Z b) { return {a.r + b.r, a.i + b.i}; }
+__device__ inline Z zscale(Z a, double s) { return {a.r * s, a.i * s}; }
+__device__ inline Z zdiv(Z a, Z b) {
+  const double d = b.r * b.r + b.i * b.i;
+  return {(a.r * b.r + a.i * b.i) / d, (a.i * b.r - a.r * b.i) / d};
+}
+__device__ inline Z zsqrt(Z a) {  // principal root, no cancellation
+  const double m = hypot(a.r, a.i);
+  if (m == 0.0) return {0.0, 0.0};
+  if (a.r >= 0.0) {
+    const double t = sqrt(0.5 * (m + a.r));
+    return {t, a.i / (2.0 * t)};
+  }
+  const double t = sqrt(0.5 * (m - a.r));
+  return {fabs(a.i) / (2.0 * t), copysign(t, a.i)};
+}
+__device__ inline Z zsinh(Z a) { return {sinh(a.r) * cos(a.i), cosh(a.r) * sin(a.i)}; }
+
+// exp(v.sigma) - I = (C - 1) I + S v.sigma with z = v.v complex, C - 1 = 2 sinh^2(r/2),
+// S = sinh(r)/r, r = sqrt(z) (series for small z); then times the scalar phase
+// exp(i phi): U - I = e (C - 1 + S v.sigma) + (e - 1) I with e - 1 = -2 sin^2(phi/2) + i sin phi.
+// Output the four entries minus the identity: d00, u01, u10, d11.
+__device__ inline void pauli_exp_general(Z v1, Z v2, Z v3, double phi, Z* d) {
+  const Z z = zadd(zadd(zmul(v1, v1), zmul(v2, v2)), zmul(v3, v3));
+  Z cm1, S;
+  if (hypot(z.r, z.i) < 1e-8) {
+    const Z z2 = zmul(z, z);
+    cm1 = zadd(zscale(z, 0.5), zscale(z2, 1.0 / 24.0));
+    S = zadd({1.0, 0.0}, zadd(zscale(z, 1.0 / 6.0), zscale(z2, 1.0 / 120.0)));
+  } else {
+    const Z r = zsqrt(z);
+    const Z sh = zsinh(zscale(r, 0.5));
+    cm1 = zscale(zmul(sh, sh), 2.0);
+    S = zdiv(zsinh(r), r);
+  }
+  // v.sigma = [[v3, v1 - i v2], [v1 + i v2, -v3]]
+  const Z iv2 = {-v2.i, v2.r};
+  Z m00 = zadd(cm1, zmul(S, v3));
+  Z m01 = zmul(S, {v1.r - iv2.r, v1.i - iv2.i});
+  Z m10 = zmul(S, {v1.r + iv2.r, v1.i + iv2.i});
+  Z m11 = zadd(cm1, zscale(zmul(S, v3), -1.0));
+  const double sh2 = sin(0.5 * phi);
+  const Z em1 = {-2.0 * sh2 * sh2, sin(phi)};  // e^{i phi} - 1
+  const Z e = {1.0 + em1.r, em1.i};
+  d[0] = zadd(zmul(e, m00), em1);
+  d[1] = zmul(e, m01);
+  d[2] = zmul(e, m10);
+  d[3] = zadd(zmul(e, m11), em1);
+}
+
+// U and U^2 with potentials (normal layout), two Q4 per point:
+// (d00.re, d00.im, u01.re, u01.im), (u10.re, u10.im, d11.re, d11.im).
+template <typename T>
+__global__ void k_halfstep_general(const double* a1, const double* a2, const double* meff,
+                                   const double* omx, const double* omy, const double* V,
+                                   const double* Ax, const double* Ay, size_t n, double dt,
+                                   Q4<T>* ug, Q4<T>* ug2) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  // exponent -i dt/2 [meff sigma_z + F], F = -i sum_j a^j Omega_j sigma_j
+  //   - sum_j a^j A_j sigma_j + V I
+  const Z v1 = {-0.5 * dt * a1[k] * omx[k], Ax ? 0.5 * dt * a1[k] * Ax[k] : 0.0};
+  const Z v2 = {-0.5 * dt * a2[k] * omy[k], Ay ? 0.5 * dt * a2[k] * Ay[k] : 0.0};
+  const Z v3 = {0.0, -0.5 * dt * meff[k]};
+  const double phi = V ? -0.5 * dt * V[k] : 0.0;
+  Z d[4];
+  pauli_exp_general(v1, v2, v3, phi, d);
+  ug[2 * k] = {(T)d[0].r, (T)d[0].i, (T)d[1].r, (T)d[1].i};
+  ug[2 * k + 1] = {(T)d[2].r, (T)d[2].i, (T)d[3].r, (T)d[3].i};
+  pauli_exp_general(zscale(v1, 2.0), zscale(v2, 2.0), zscale(v3, 2.0), 2.0 * phi, d);
+  ug2[2 * k] = {(T)d[0].r, (T)d[0].i, (T)d[1].r, (T)d[1].i};
+  ug2[2 * k + 1] = {(T)d[2].r, (T)d[2].i, (T)d[3].r, (T)d[3].i};
+}
+
+template <typename T>
+cudaError_t launch_halfstep_general(const double* a1, const double* a2, const double* meff,
+                                    const double* omx, const double* omy, const double* V,
+                                    const double* Ax, const double* Ay, int nx, int ny,
+                                    double dt, Q4<T>* ug, Q4<T>* ug2, cudaStream_t st) {
+  const size_t n = (size_t)nx * ny;
+  k_halfstep_general<T><<<nblocks(n), TPB, 0, st>>>(a1, a2, meff, omx, omy, V, Ax, Ay, n, dt,
+                                                    ug, ug2);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_halfstep(const double* a1, const double* a2, const double* meff,
                             const double* omx, const double* omy, int nx, int ny, double dt,
@@ -289,6 +379,10 @@ cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cu
   template cudaError_t launch_halfstep<T>(const double*, const double*, const double*,      \
                                           const double*, const double*, int, int, double,    \
                                           Q4<T>*, Q4<T>*, Q4<T>*, Q4<T>*, cudaStream_t);     \
+  template cudaError_t launch_halfstep_general<T>(                                            \
+      const double*, const double*, const double*, const double*, const double*,             \
+      const double*, const double*, const double*, int, int, double, Q4<T>*, Q4<T>*,         \
+      cudaStream_t);                                                                         \
   template cudaError_t launch_twiddles<T>(int, int, Cx<T>*, cudaStream_t);                    \
   template cudaError_t launch_step_mult<T>(int, double, double, Q4<T>*, cudaStream_t);        \
   template cudaError_t launch_deriv_mult<T>(int, double, Q4<T>*, cudaStream_t);               \

@@ -22,6 +22,21 @@ __global__ void k_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n) {
   if (k < n) psi[k] = apply_u(u[k], psi[k]);
 }
 
+// psi <- U psi for a general complex U stored as two Q4 per point (deviation from I):
+// (d00, u01), (u10, d11)
+template <typename T>
+__global__ void k_apply_ug(Q4<T>* psi, const Q4<T>* ug, size_t n) {
+  const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const Q4<T> p = psi[k], r0 = ug[2 * k], r1 = ug[2 * k + 1];
+  // row 0: d00 psi1 + u01 psi2; row 1: u10 psi1 + d11 psi2 (complex), added to psi
+  const T a = p.x, b = p.y, c = p.z, d = p.w;
+  psi[k] = {a + (r0.x * a - r0.y * b + r0.z * c - r0.w * d),
+            b + (r0.x * b + r0.y * a + r0.z * d + r0.w * c),
+            c + (r1.x * a - r1.y * b + r1.z * c - r1.w * d),
+            d + (r1.x * b + r1.y * a + r1.z * d + r1.w * c)};
+}
+
 // S = b1 sigma_x dx + b2 sigma_y dy with sigma_x (u, v) = (v, u), sigma_y (u, v) =
 // (-i v, i u); out = alpha S + beta prev; acc += gamma out.
 template <typename T>
@@ -172,6 +187,12 @@ cudaError_t launch_axpby(Q4<T>* out, double a, const Q4<T>* x, double b, const Q
 }
 
 template <typename T>
+cudaError_t launch_apply_ug(Q4<T>* psi, const Q4<T>* ug, size_t n, cudaStream_t st) {
+  k_apply_ug<T><<<blocks_for(n), TPB, 0, st>>>(psi, ug, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n, cudaStream_t st) {
   k_apply_u<T><<<blocks_for(n), TPB, 0, st>>>(psi, u, n);
   return cudaGetLastError();
@@ -237,6 +258,7 @@ bool bessel_j_series(double x, int n, double* out) {
 
 #define INST(T)                                                                              \
   template cudaError_t launch_apply_u<T>(Q4<T>*, const Q4<T>*, size_t, cudaStream_t);        \
+  template cudaError_t launch_apply_ug<T>(Q4<T>*, const Q4<T>*, size_t, cudaStream_t);       \
   template cudaError_t launch_unsplit_combine<T>(                                            \
       const Q4<T>*, const Q4<T>*, const double*, const double*, const double*, const double*, \
       int, int, double, double, const Q4<T>*, double, double, double, Q4<T>*, Q4<T>*,       \
