@@ -46,7 +46,7 @@ typedef enum {
   DIRAC_OK = 0,
   DIRAC_EINVAL = 1,       /* invalid argument (sizes, pointers, non-positive g, dt <= 0) */
   DIRAC_ENOMEM = 2,       /* device or host allocation failed                           */
-  DIRAC_EUNSUPPORTED = 3, /* valid but outside this build (e.g. theta != 0)              */
+  DIRAC_EUNSUPPORTED = 3, /* valid but outside this build (e.g. theta != 0 in complex64) */
   DIRAC_ECUDA = 4,        /* a CUDA runtime call failed                                   */
   DIRAC_ETIMEOUT = 5,     /* a bounded device wait ran out                                */
   DIRAC_ENONFINITE = 6,   /* the state holds NaN or Inf                                   */
@@ -103,7 +103,9 @@ typedef struct {
 
 /* Absorbing layer (Sec. 3): width_x/width_y grid points per side (0 = none, < N/2),
  * type 1..6 = the paper's profiles I..VI, sigma0 = Sigma_0, theta = stretching angle.
- * theta != 0 makes b complex and returns DIRAC_EUNSUPPORTED in this build. */
+ * theta != 0 (S = 1 + exp(i theta) Sigma~) makes b complex: supported in complex128 (the
+ * passes add i Im(b - 1) D); complex64 contexts return DIRAC_EUNSUPPORTED, as do batches
+ * of such contexts. */
 typedef struct {
   int width_x, width_y;
   int type;

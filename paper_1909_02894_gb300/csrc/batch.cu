@@ -337,8 +337,9 @@ dirac_status dirac_batch_submit(dirac_batch* b, dirac_ctx* inst, long n_steps, d
   if (!inst->state_set) return bfail(b, DIRAC_ESTATE, "set_state must come before submit");
   if (inst->scheme != DIRAC_SCHEME_II)
     return bfail(b, DIRAC_EUNSUPPORTED, "the batch runs the printed sub-step order only");
-  if (inst->has_pot)
-    return bfail(b, DIRAC_EUNSUPPORTED, "the batch runs without static potentials");
+  if (inst->has_pot || inst->beta1_im)
+    return bfail(b, DIRAC_EUNSUPPORTED,
+                 "the batch runs without static potentials and complex stretching");
   if (n_steps < 1) return bfail(b, DIRAC_EINVAL, "n_steps must be >= 1");
   if (!(dt > 0.0)) return bfail(b, DIRAC_EINVAL, "dt must be positive");
   for (const Slot& s : b->slots)

@@ -22,9 +22,11 @@ struct dirac_ctx {
   double *a1 = nullptr, *a2 = nullptr, *meff = nullptr, *w = nullptr, *omx = nullptr,
          *omy = nullptr;
   double *sxinv = nullptr, *syinv = nullptr;
+  double *sxinv_im = nullptr, *syinv_im = nullptr;  // complex stretching (theta != 0)
   // state and per-pass coefficients in the state precision
   void *psi = nullptr, *psiT = nullptr;
   void *beta1 = nullptr, *beta2T = nullptr;
+  void *beta1_im = nullptr, *beta2T_im = nullptr;  // complex stretching: Im(b - 1)
   void *u_n = nullptr, *u_t = nullptr, *u2_t = nullptr;
   void *tw_x = nullptr, *tw_y = nullptr, *mult_x = nullptr, *mult_y = nullptr,
        *dmult_x = nullptr, *dmult_y = nullptr;

@@ -158,8 +158,10 @@ static dirac_status step_symmetric(dirac_ctx* ctx, long n) {
   LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
   ax.mult = (const Q4<T>*)ctx->mult_xh;
   ax.beta = (const T*)ctx->beta1;
+  ax.beta_im = (const T*)ctx->beta1_im;
   ay.mult = (const Q4<T>*)ctx->mult_y;
   ay.beta = (const T*)ctx->beta2T;
+  ay.beta_im = (const T*)ctx->beta2T_im;
   ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
   ctx->test_timeout_next = 0;
   void* cur = ctx->psi;
@@ -223,7 +225,8 @@ static dirac_status unsplit_apply(dirac_ctx* ctx, const void* in, void* out, dou
   ay.mult = (const Q4<T>*)ctx->dmult_y;
   CK(launch_line_pass<T>(ay, MODE_DERIV, 0, st), "y derivative");
   CK(launch_unsplit_combine<T>((const Q4<T>*)ctx->scratch1, (const Q4<T>*)ctx->scratch2, ctx->a1,
-                               ctx->a2, ctx->sxinv, ctx->syinv, ctx->nx, ctx->ny, ar, ai,
+                               ctx->a2, ctx->sxinv, ctx->syinv, ctx->sxinv_im, ctx->syinv_im,
+                               ctx->nx, ctx->ny, ar, ai,
                                (const Q4<T>*)prev, beta, gr, gi, (Q4<T>*)out, (Q4<T>*)acc, st),
      "combine");
   ctx->launches += 4;
@@ -256,7 +259,8 @@ static dirac_status step_poly(dirac_ctx* ctx, long n, double dt) {
       const int nb = 256;
       double* part = nullptr;
       CK(dalloc(ctx, (void**)&part, 2 * nb * sizeof(double)), "scratch");
-      CK(launch_max_b(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, ctx->nx, ctx->ny, part, nb, st),
+      CK(launch_max_b(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, ctx->sxinv_im, ctx->syinv_im,
+                      ctx->nx, ctx->ny, part, nb, st),
          "max b");
       std::vector<double> h(2 * nb);
       CK(cudaMemcpyAsync(h.data(), part, 2 * nb * sizeof(double), cudaMemcpyDeviceToHost, st),
@@ -485,10 +489,12 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   ax.out = (Q4<T>*)ctx->psiT;
   ax.mult = (const Q4<T>*)ctx->mult_x;
   ax.beta = (const T*)ctx->beta1;
+  ax.beta_im = (const T*)ctx->beta1_im;
   ay.in = (const Q4<T>*)ctx->psiT;
   ay.out = (Q4<T>*)ctx->psi;
   ay.mult = (const Q4<T>*)ctx->mult_y;
   ay.beta = (const T*)ctx->beta2T;
+  ay.beta_im = (const T*)ctx->beta2T_im;
   ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
   ctx->test_timeout_next = 0;
   const bool fused = !ctx->has_pot;  // potentials: U applied by its own kernel
@@ -583,11 +589,21 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
   for (double** p : f64) CK(dalloc(ctx, (void**)p, n * sizeof(double)), "allocate fields");
   CK(dalloc(ctx, (void**)&ctx->sxinv, nx * sizeof(double)), "allocate layer");
   CK(dalloc(ctx, (void**)&ctx->syinv, ny * sizeof(double)), "allocate layer");
+  const bool complex_layer =
+      ctx->abs.theta != 0.0 && (ctx->abs.width_x > 0 || ctx->abs.width_y > 0);
+  if (complex_layer) {
+    CK(dalloc(ctx, (void**)&ctx->sxinv_im, nx * sizeof(double)), "allocate layer");
+    CK(dalloc(ctx, (void**)&ctx->syinv_im, ny * sizeof(double)), "allocate layer");
+  }
   // state, coefficient fields, tables
   CK(dalloc(ctx, &ctx->psi, n * sizeof(Q4<T>)), "allocate state");
   CK(dalloc(ctx, &ctx->psiT, n * sizeof(Q4<T>)), "allocate state");
   CK(dalloc(ctx, &ctx->beta1, n * sizeof(T)), "allocate coefficients");
   CK(dalloc(ctx, &ctx->beta2T, n * sizeof(T)), "allocate coefficients");
+  if (complex_layer) {
+    CK(dalloc(ctx, &ctx->beta1_im, n * sizeof(T)), "allocate coefficients");
+    CK(dalloc(ctx, &ctx->beta2T_im, n * sizeof(T)), "allocate coefficients");
+  }
   if (!ctx->u_identity) {
     CK(dalloc(ctx, &ctx->u_n, n * sizeof(Q4<T>)), "allocate half-step");
     CK(dalloc(ctx, &ctx->u_t, n * sizeof(Q4<T>)), "allocate half-step");
@@ -658,12 +674,15 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
   CK(cudaFreeAsync(logs, st), "free"); CK(cudaFreeAsync(logsT, st), "free");
   CK(cudaFreeAsync(dxT, st), "free"); CK(cudaFreeAsync(dy, st), "free");
   // absorbing layer and b - 1
-  CK(launch_pml(nx, ctx->ax, ctx->abs.width_x, ctx->abs.type, ctx->abs.sigma0, ctx->sxinv, st),
+  CK(launch_pml(nx, ctx->ax, ctx->abs.width_x, ctx->abs.type, ctx->abs.sigma0, ctx->abs.theta,
+                ctx->sxinv, ctx->sxinv_im, st),
      "layer x");
-  CK(launch_pml(ny, ctx->ay, ctx->abs.width_y, ctx->abs.type, ctx->abs.sigma0, ctx->syinv, st),
+  CK(launch_pml(ny, ctx->ay, ctx->abs.width_y, ctx->abs.type, ctx->abs.sigma0, ctx->abs.theta,
+                ctx->syinv, ctx->syinv_im, st),
      "layer y");
-  CK(launch_beta<T>(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, nx, ny, (T*)ctx->beta1,
-                    (T*)ctx->beta2T, st),
+  CK(launch_beta<T>(ctx->a1, ctx->a2, ctx->sxinv, ctx->syinv, ctx->sxinv_im, ctx->syinv_im, nx,
+                    ny, (T*)ctx->beta1, (T*)ctx->beta2T, (T*)ctx->beta1_im,
+                    (T*)ctx->beta2T_im, st),
      "b - 1");
   CK(launch_twiddles<T>(nx, line_pass_radix<T>(nx), (Cx<T>*)ctx->tw_x, st), "twiddles");
   CK(launch_twiddles<T>(ny, line_pass_radix<T>(ny), (Cx<T>*)ctx->tw_y, st), "twiddles");
@@ -791,8 +810,9 @@ dirac_status dirac_create(const dirac_grid* grid, const dirac_domain* domain,
       return fail(nullptr, DIRAC_EINVAL, "absorber type must be 1..6");
     if (!isfinite(ab.sigma0) || ab.sigma0 < 0.0 || !isfinite(ab.theta))
       return fail(nullptr, DIRAC_EINVAL, "absorber sigma0 must be >= 0 and theta finite");
-    if (ab.theta != 0.0 && (ab.width_x > 0 || ab.width_y > 0))
-      return fail(nullptr, DIRAC_EUNSUPPORTED, "complex stretching (theta != 0) is not built");
+    if (ab.theta != 0.0 && (ab.width_x > 0 || ab.width_y > 0) && precision != DIRAC_C128)
+      return fail(nullptr, DIRAC_EUNSUPPORTED,
+                  "complex stretching (theta != 0) needs complex128 (a complex b)");
   }
   int conn = DIRAC_CONN_COVARIANT;
   const double* g_host[3] = {nullptr, nullptr, nullptr};

@@ -34,13 +34,17 @@ cudaError_t launch_metric_fields(const double* g00, const double* g11, const dou
 // the y derivative (normal layout) of the log fields.
 cudaError_t launch_omega(const Q4<double>* dxT, const Q4<double>* dy, int nx, int ny,
                          double fac, double* omx, double* omy, cudaStream_t st);
-// 1/S for grid indices of one axis (Sec. 3 profiles), real (theta = 0).
-cudaError_t launch_pml(int n, double a, int width, int type, double sigma0, double* sinv,
-                       cudaStream_t st);
-// beta1 = a1/S1 - 1 (normal layout), beta2T = a2/S2 - 1 (transposed layout), in T.
+// 1/S for grid indices of one axis (Sec. 3 profiles), S = 1 + exp(i theta) Sigma~: the real
+// part into sinv and, if sinv_im is not null, the imaginary part (else theta must be 0).
+cudaError_t launch_pml(int n, double a, int width, int type, double sigma0, double theta,
+                       double* sinv, double* sinv_im, cudaStream_t st);
+// beta1 = a1/S1 - 1 (normal layout), beta2T = a2/S2 - 1 (transposed layout), in T; with
+// complex stretching (sxinv_im, syinv_im not null) the imaginary parts go to beta1_im,
+// beta2T_im.
 template <typename T>
 cudaError_t launch_beta(const double* a1, const double* a2, const double* sxinv,
-                        const double* syinv, int nx, int ny, T* beta1, T* beta2T,
+                        const double* syinv, const double* sxinv_im, const double* syinv_im,
+                        int nx, int ny, T* beta1, T* beta2T, T* beta1_im, T* beta2T_im,
                         cudaStream_t st);
 // Half-step matrices for dt: U (normal layout), U and U^2 (transposed layout) and, if
 // u2_n is not null, U^2 in the normal layout, stored as (c0 - 1, c1, c2, c3) in T.
@@ -74,11 +78,13 @@ cudaError_t launch_apply_ug(Q4<T>* psi, const Q4<T>* ug, size_t n, cudaStream_t 
 template <typename T>
 cudaError_t launch_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n, cudaStream_t st);
 // out = alpha (b1 sigma_x dx + b2 sigma_y dy) + beta prev (prev may be null); acc +=
-// gamma out (acc may be null); b^j = a^j / S^j from the FP64 fields; all normal layout.
+// gamma out (acc may be null); b^j = a^j / S^j from the FP64 fields (complex when the
+// imaginary parts of 1/S are given); all normal layout.
 template <typename T>
 cudaError_t launch_unsplit_combine(const Q4<T>* dx, const Q4<T>* dy, const double* a1,
                                    const double* a2, const double* sxinv, const double* syinv,
-                                   int nx, int ny, double ar, double ai, const Q4<T>* prev,
+                                   const double* sxinv_im, const double* syinv_im, int nx,
+                                   int ny, double ar, double ai, const Q4<T>* prev,
                                    double beta, double gr, double gi, Q4<T>* out, Q4<T>* acc,
                                    cudaStream_t st);
 // out = c in.
@@ -87,8 +93,8 @@ cudaError_t launch_scale(Q4<T>* out, const Q4<T>* in, double cr, double ci, size
                          cudaStream_t st);
 // Per-block maxima of |b1|, |b2| into partials[2 * n_blocks].
 cudaError_t launch_max_b(const double* a1, const double* a2, const double* sxinv,
-                         const double* syinv, int nx, int ny, double* partials,
-                         int n_blocks, cudaStream_t st);
+                         const double* syinv, const double* sxinv_im, const double* syinv_im,
+                         int nx, int ny, double* partials, int n_blocks, cudaStream_t st);
 // Krylov building blocks (Scheme I). Partial inner products <V_i, w> (i < count) in
 // FP64: partials[2 (i n_blocks + b)] (re, im) per block b; V is a device array of count
 // pointers.

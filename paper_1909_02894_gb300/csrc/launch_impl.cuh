@@ -104,7 +104,7 @@ static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st)
   using PG = PGeo<float, L>;
   // one U field per pass: the U landing zone holds either the load-side or the
   // store-side matrices (batched launches keep the same rule per instance)
-  if (!a.err || a.n_lines % PG::GL != 0 || (a.u_load && a.u_store)) return cudaErrorInvalidValue;
+  if (!a.err || a.n_lines % PG::GL != 0 || (a.u_load && a.u_store) || a.beta_im) return cudaErrorInvalidValue;
   auto kern = a.inst ? line_pass_persistent<float, L, true> : line_pass_persistent<float, L, false>;
   static int max_clusters[2][64] = {};
   int dev = 0;

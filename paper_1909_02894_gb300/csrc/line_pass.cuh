@@ -57,6 +57,7 @@ struct LinePassArgs {
   const Q4<T>* mult;    // per k index q: step ((cos - 1) hi, lo, sin hi, lo) / (2L);
                         // derivative (0, 0, xi hi, xi lo) / L
   const T* beta;        // b - 1 per input point, or nullptr (b = 1)
+  const T* beta_im;     // imaginary part of b - 1 (complex stretching), or nullptr
   const Q4<T>* u_load;  // U applied to psi when it is read, or nullptr
   const Q4<T>* u_store; // U applied to psi_new before the store, or nullptr
   int* err;             // device error flag (persistent variant: bounded-wait timeouts)
@@ -500,6 +501,10 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
       const T bm1 = a.beta ? a.beta[gi] : T(0);
       Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+      if (a.beta_im) {  // complex b - 1: add i Im(b - 1) d
+        const T bi = a.beta_im[gi];
+        o = {o.re - bi * d.im, o.im + bi * d.re};
+      }
       if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
       if (a.store_normal) reinterpret_cast<Cx<T>*>(a.out)[2 * gi + c] = o;
       else my_stage[2 * i] = o;

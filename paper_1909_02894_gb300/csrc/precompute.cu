@@ -67,10 +67,11 @@ cudaError_t launch_omega(const Q4<double>* dxT, const Q4<double>* dy, int nx, in
 // right; with s = e - delta (delta = width h) the six profiles are
 // s0 e^2, s0 e^3, -s0/s, s0/s^2, -s0/s - s0/delta, s0/s^2 - s0/delta^2.
 // Where a singular profile is infinite, 1/S = 0.
-__global__ void k_pml(int n, double a, int width, int type, double sigma0, double* sinv) {
+__global__ void k_pml(int n, double a, int width, int type, double sigma0, double theta,
+                      double* sinv, double* sinv_im) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double r = 1.0;
+  double r = 1.0, ri = 0.0;
   if (width > 0 && (i <= width || i >= n - width)) {
     const double h = 2.0 * a / n;
     const double depth = (i <= width) ? (double)(width - i) * h : (double)(i - n + width) * h;
@@ -87,33 +88,48 @@ __global__ void k_pml(int n, double a, int width, int type, double sigma0, doubl
       case 6: inf = (s == 0.0); if (!inf) sig = sigma0 / (s * s) - sigma0 / (delta * delta); break;
       default: break;
     }
-    r = inf ? 0.0 : 1.0 / (1.0 + sig);
+    if (sinv_im) {  // S = 1 + exp(i theta) Sigma~, 1/S = conj(S) / |S|^2
+      const double sr = 1.0 + cos(theta) * sig, si = sin(theta) * sig;
+      const double m = sr * sr + si * si;
+      r = inf ? 0.0 : sr / m;
+      ri = inf ? 0.0 : -si / m;
+    } else {
+      r = inf ? 0.0 : 1.0 / (1.0 + sig);
+    }
   }
   sinv[i] = r;
+  if (sinv_im) sinv_im[i] = ri;
 }
 
-cudaError_t launch_pml(int n, double a, int width, int type, double sigma0, double* sinv,
-                       cudaStream_t st) {
-  k_pml<<<nblocks(n), TPB, 0, st>>>(n, a, width, type, sigma0, sinv);
+cudaError_t launch_pml(int n, double a, int width, int type, double sigma0, double theta,
+                       double* sinv, double* sinv_im, cudaStream_t st) {
+  k_pml<<<nblocks(n), TPB, 0, st>>>(n, a, width, type, sigma0, theta, sinv, sinv_im);
   return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void k_beta(const double* a1, const double* a2, const double* sxinv,
-                       const double* syinv, int nx, int ny, T* beta1, T* beta2T) {
+                       const double* syinv, const double* sxinv_im, const double* syinv_im,
+                       int nx, int ny, T* beta1, T* beta2T, T* beta1_im, T* beta2T_im) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nx * ny) return;
   const int j = k / nx, i = k - j * nx;
   beta1[k] = (T)(a1[k] * sxinv[i] - 1.0);
   beta2T[(size_t)i * ny + j] = (T)(a2[k] * syinv[j] - 1.0);
+  if (beta1_im) {  // complex stretching: imaginary parts of b - 1
+    beta1_im[k] = (T)(a1[k] * sxinv_im[i]);
+    beta2T_im[(size_t)i * ny + j] = (T)(a2[k] * syinv_im[j]);
+  }
 }
 
 template <typename T>
 cudaError_t launch_beta(const double* a1, const double* a2, const double* sxinv,
-                        const double* syinv, int nx, int ny, T* beta1, T* beta2T,
+                        const double* syinv, const double* sxinv_im, const double* syinv_im,
+                        int nx, int ny, T* beta1, T* beta2T, T* beta1_im, T* beta2T_im,
                         cudaStream_t st) {
-  k_beta<T><<<nblocks((size_t)nx * ny), TPB, 0, st>>>(a1, a2, sxinv, syinv, nx, ny, beta1,
-                                                      beta2T);
+  k_beta<T><<<nblocks((size_t)nx * ny), TPB, 0, st>>>(a1, a2, sxinv, syinv, sxinv_im, syinv_im,
+                                                      nx, ny, beta1, beta2T, beta1_im,
+                                                      beta2T_im);
   return cudaGetLastError();
 }
 
@@ -375,7 +391,8 @@ cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cu
 
 #define INST(T)                                                                              \
   template cudaError_t launch_beta<T>(const double*, const double*, const double*,          \
-                                      const double*, int, int, T*, T*, cudaStream_t);        \
+                                      const double*, const double*, const double*, int, int, \
+                                      T*, T*, T*, T*, cudaStream_t);        \
   template cudaError_t launch_halfstep<T>(const double*, const double*, const double*,      \
                                           const double*, const double*, int, int, double,    \
                                           Q4<T>*, Q4<T>*, Q4<T>*, Q4<T>*, cudaStream_t);     \

@@ -39,18 +39,26 @@ __global__ void k_apply_ug(Q4<T>* psi, const Q4<T>* ug, size_t n) {
 
 // S = b1 sigma_x dx + b2 sigma_y dy with sigma_x (u, v) = (v, u), sigma_y (u, v) =
 // (-i v, i u); out = alpha S + beta prev; acc += gamma out.
+// b^j complex with complex stretching (sxinv_im, syinv_im not null).
 template <typename T>
 __global__ void k_unsplit_combine(const Q4<T>* dx, const Q4<T>* dy, const double* a1,
                                   const double* a2, const double* sxinv, const double* syinv,
-                                  int nx, int ny, T ar, T ai, const Q4<T>* prev, T beta, T gr,
-                                  T gi, Q4<T>* out, Q4<T>* acc) {
+                                  const double* sxinv_im, const double* syinv_im, int nx,
+                                  int ny, T ar, T ai, const Q4<T>* prev, T beta, T gr, T gi,
+                                  Q4<T>* out, Q4<T>* acc) {
   const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= (size_t)nx * ny) return;
   const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
   const T b1 = (T)(a1[k] * sxinv[i]), b2 = (T)(a2[k] * syinv[j]);
+  const T b1i = sxinv_im ? (T)(a1[k] * sxinv_im[i]) : T(0);
+  const T b2i = syinv_im ? (T)(a2[k] * syinv_im[j]) : T(0);
   const Q4<T> x = dx[k], y = dy[k];
-  const T s1r = b1 * x.z + b2 * y.w, s1i = b1 * x.w - b2 * y.z;
-  const T s2r = b1 * x.x - b2 * y.y, s2i = b1 * x.y + b2 * y.x;
+  // sigma_x dx = (dx2, dx1), sigma_y dy = (-i dy2, i dy1), times complex b
+  const T t1r = y.w, t1i = -y.z, t2r = -y.y, t2i = y.x;  // sigma_y dy components
+  const T s1r = (b1 * x.z - b1i * x.w) + (b2 * t1r - b2i * t1i);
+  const T s1i = (b1 * x.w + b1i * x.z) + (b2 * t1i + b2i * t1r);
+  const T s2r = (b1 * x.x - b1i * x.y) + (b2 * t2r - b2i * t2i);
+  const T s2i = (b1 * x.y + b1i * x.x) + (b2 * t2i + b2i * t2r);
   Q4<T> o = {ar * s1r - ai * s1i, ar * s1i + ai * s1r, ar * s2r - ai * s2i, ar * s2i + ai * s2r};
   if (prev) {
     const Q4<T> p = prev[k];
@@ -81,15 +89,16 @@ __global__ void k_scale(Q4<T>* out, const Q4<T>* in, T cr, T ci, size_t n) {
 
 // Per-block maxima of |b1| and |b2| (grid-stride), partials[2 b], partials[2 b + 1].
 __global__ void k_max_b(const double* a1, const double* a2, const double* sxinv,
-                        const double* syinv, int nx, int ny, double* partials) {
+                        const double* syinv, const double* sxinv_im, const double* syinv_im,
+                        int nx, int ny, double* partials) {
   __shared__ double m1[TPB], m2[TPB];
   double x1 = 0.0, x2 = 0.0;
   const size_t n = (size_t)nx * ny;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(k / nx), i = (int)(k - (size_t)j * nx);
-    x1 = fmax(x1, fabs(a1[k] * sxinv[i]));
-    x2 = fmax(x2, fabs(a2[k] * syinv[j]));
+    x1 = fmax(x1, fabs(a1[k]) * hypot(sxinv[i], sxinv_im ? sxinv_im[i] : 0.0));
+    x2 = fmax(x2, fabs(a2[k]) * hypot(syinv[j], syinv_im ? syinv_im[j] : 0.0));
   }
   m1[threadIdx.x] = x1;
   m2[threadIdx.x] = x2;
@@ -201,11 +210,13 @@ cudaError_t launch_apply_u(Q4<T>* psi, const Q4<T>* u, size_t n, cudaStream_t st
 template <typename T>
 cudaError_t launch_unsplit_combine(const Q4<T>* dx, const Q4<T>* dy, const double* a1,
                                    const double* a2, const double* sxinv, const double* syinv,
-                                   int nx, int ny, double ar, double ai, const Q4<T>* prev,
+                                   const double* sxinv_im, const double* syinv_im, int nx,
+                                   int ny, double ar, double ai, const Q4<T>* prev,
                                    double beta, double gr, double gi, Q4<T>* out, Q4<T>* acc,
                                    cudaStream_t st) {
   k_unsplit_combine<T><<<blocks_for((size_t)nx * ny), TPB, 0, st>>>(
-      dx, dy, a1, a2, sxinv, syinv, nx, ny, (T)ar, (T)ai, prev, (T)beta, (T)gr, (T)gi, out, acc);
+      dx, dy, a1, a2, sxinv, syinv, sxinv_im, syinv_im, nx, ny, (T)ar, (T)ai, prev, (T)beta,
+      (T)gr, (T)gi, out, acc);
   return cudaGetLastError();
 }
 
@@ -217,9 +228,9 @@ cudaError_t launch_scale(Q4<T>* out, const Q4<T>* in, double cr, double ci, size
 }
 
 cudaError_t launch_max_b(const double* a1, const double* a2, const double* sxinv,
-                         const double* syinv, int nx, int ny, double* partials,
-                         int n_blocks, cudaStream_t st) {
-  k_max_b<<<n_blocks, TPB, 0, st>>>(a1, a2, sxinv, syinv, nx, ny, partials);
+                         const double* syinv, const double* sxinv_im, const double* syinv_im,
+                         int nx, int ny, double* partials, int n_blocks, cudaStream_t st) {
+  k_max_b<<<n_blocks, TPB, 0, st>>>(a1, a2, sxinv, syinv, sxinv_im, syinv_im, nx, ny, partials);
   return cudaGetLastError();
 }
 
@@ -261,8 +272,8 @@ bool bessel_j_series(double x, int n, double* out) {
   template cudaError_t launch_apply_ug<T>(Q4<T>*, const Q4<T>*, size_t, cudaStream_t);       \
   template cudaError_t launch_unsplit_combine<T>(                                            \
       const Q4<T>*, const Q4<T>*, const double*, const double*, const double*, const double*, \
-      int, int, double, double, const Q4<T>*, double, double, double, Q4<T>*, Q4<T>*,       \
-      cudaStream_t);                                                                         \
+      const double*, const double*, int, int, double, double, const Q4<T>*, double, double,  \
+      double, Q4<T>*, Q4<T>*, cudaStream_t);                                                 \
   template cudaError_t launch_scale<T>(Q4<T>*, const Q4<T>*, double, double, size_t,         \
                                        cudaStream_t);                                        \
   template cudaError_t launch_multi_dot<T>(const Q4<T>* const*, int, const Q4<T>*, size_t,    \

@@ -47,7 +47,7 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     (dict(mass=float("nan")), D.DIRAC_EINVAL),
     (dict(pml_wx=16), D.DIRAC_EINVAL),               # width >= N/2
     (dict(pml_wx=4, pml_type=7), D.DIRAC_EINVAL),
-    (dict(pml_wx=4, theta=0.3), D.DIRAC_EUNSUPPORTED),
+    (dict(pml_wx=4, theta=0.3), D.DIRAC_EUNSUPPORTED),  # complex layer in complex64
     (dict(precision=5), D.DIRAC_EINVAL),
     (dict(conn=9), D.DIRAC_EINVAL),
     (dict(g11=-np.ones((32, 32))), D.DIRAC_EINVAL),  # non-positive metric
