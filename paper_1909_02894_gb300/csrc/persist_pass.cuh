@@ -63,7 +63,9 @@ struct PGeo {
   static constexpr size_t OFF_BETA = OFF_PSI + PSI_BYTES;
   static constexpr size_t OFF_U = OFF_BETA + CHUNKS * BETA_PITCH;
   static constexpr size_t OFF_BAR = OFF_U + CHUNKS * U_PITCH;
-  static constexpr size_t SMEM = OFF_BAR + 32;  // two mbarriers + tensor-memory address
+  static constexpr size_t OFF_T3 = OFF_BAR + 32;  // two mbarriers + tensor-memory address
+  // pass-3 twiddles of the digit-swap FFT: 8 warp slices x 8 entries (the 7 powers, a pad)
+  static constexpr size_t SMEM = OFF_T3 + 64 * sizeof(Cx<T>);
   // tensor memory: 8 warps share each lane quarter; per warp slice s = warp / 4 the
   // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds an
   // exchange region of 128 columns and 32 twiddle columns per slice
@@ -149,12 +151,12 @@ __device__ __forceinline__ void tmem_swap(Cx<T> (&v)[8], uint32_t x, int s, int 
 
 // tws: this thread's pass-1 and pass-2 twiddles parked in tensor memory (w^1..w^7 of
 // each, 16 columns apart); x: the exchange region; fc: this component's 4096-point shared
-// buffer and cx its slot XOR (0 or 9, see swz4096); tw: the pass table (pass 3's twiddles
-// depend on the slice only: one cached line per warp).
+// buffer and cx its slot XOR (0 or 9, see swz4096); t3: the warp slice's pass-3 twiddles
+// W_64^(d0 t), t = 1..7, in shared memory (one broadcast read each).
 template <typename T, bool INV>
 __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, int j, int s,
                                              int q, uint32_t tws, uint32_t x,
-                                             const Cx<T>* tw) {
+                                             const Cx<T>* t3) {
   {
     float t1[16];
     tmem_ld16(tws, t1);
@@ -190,11 +192,10 @@ __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, i
   for (int r = 0; r < 8; ++r) v[r] = fc[(r & 1 ? rb1 : rb0) + 8 * r];
   dft8<T, INV>(v);
   {
-    const Cx<T>* t3 = tw + tw_offset(8, 8) + hi;  // block of span 8: [(t - 1) 8 + k]
     float f[16];
 #pragma unroll
     for (int t = 1; t < 8; ++t) {
-      const Cx<T> w = ldg_cx(t3 + 8 * (t - 1));
+      const Cx<T> w = t3[t - 1];
       f[2 * t - 2] = w.re;
       f[2 * t - 1] = w.im;
     }
@@ -222,6 +223,7 @@ __global__ void __launch_bounds__(1024, 1)
   Q4<T>* u_z = reinterpret_cast<Q4<T>*>(psmem + PG::OFF_U);
   uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::OFF_BAR);  // [0] spinor, [1] b-1/U
   uint32_t* tslot = reinterpret_cast<uint32_t*>(psmem + PG::OFF_BAR + 2 * sizeof(uint64_t));
+  Cx<T>* t3tab = reinterpret_cast<Cx<T>*>(psmem + PG::OFF_T3);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
@@ -285,6 +287,13 @@ __global__ void __launch_bounds__(1024, 1)
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     fence_mbar_init();
+  }
+  if constexpr (PG::SWAP) {
+    // pass-3 twiddles W_64^(s t) (block of span 8 of the pass table: [(t - 1) 8 + s])
+    if (tid < 56) {
+      const int s3 = tid / 7, t = tid - s3 * 7 + 1;
+      t3tab[s3 * 8 + t - 1] = ldg_cx(a0.tw + tw_offset(8, 8) + (t - 1) * 8 + s3);
+    }
   }
   if (warp == 0) tmem_alloc(tslot, PG::TMEM_COLS);
   tmem_fence_before_sync();
@@ -396,7 +405,8 @@ __global__ void __launch_bounds__(1024, 1)
     if (!failed) {
       if constexpr (PG::SWAP)
         fft4096_swap<T, false>(v, fbuf + c * L, 9 * c, j, slice, quarter,
-                               tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X, a.tw);
+                               tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
+                               t3tab + 8 * slice);
       else
         fft_passes<T, L, E, false>(v, buf, j, a.tw);
 #pragma unroll
@@ -422,7 +432,8 @@ __global__ void __launch_bounds__(1024, 1)
         __syncthreads();
         tmem_fence_after_sync();
         fft4096_swap<T, true>(v, fbuf + c * L, 9 * c, j2, slice, quarter,
-                              tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X, a.tw);
+                              tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
+                              t3tab + 8 * slice);
       }
       else
         fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
