@@ -344,8 +344,14 @@ def run_serve(args):
                      "elapsed_s": elapsed, "max_active": srv.max_active,
                      "admitted_while_busy": srv.admitted_while_busy, "ticks": srv.ticks})
         checks = S.fp64_check(results, stream=stream.cuda_stream)
-        summ["fp64_check"] = {"requests": len(checks),
-                              "max_rel_l2": max((c["rel_l2"] for c in checks), default=None)}
+        summ["fp64_check"] = {
+            "requests": len(checks),
+            "max_rel_l2": max((c["rel_l2"] for c in checks), default=None),
+            "max_err_vs_initial_norm": max((c["err_vs_initial_norm"] for c in checks),
+                                           default=None),
+            "min_kept_norm": min((c["kept_norm"] for c in checks), default=None),
+            "checks": [{k: c[k] for k in ("n", "steps", "rel_l2", "err_vs_initial_norm",
+                                          "kept_norm")} for c in checks]}
         out[label] = summ
     line = {
         "metric": "p50/p99 solve ms and grid-point*steps/s (serving)",
