@@ -59,3 +59,24 @@ def test_fp64_check_of_served_requests():
     checks = S.fp64_check(results)
     assert len(checks) == len(reqs) > 0
     assert all(c["rel_l2"] <= 1e-5 for c in checks), checks
+
+
+def test_served_large_grids_equal_alone_runs():
+    """The serving sizes above 256^2 (persistent passes: 512-, 1024- and 2048-point lines)
+    running together in one batch give the alone results bit for bit."""
+    D.build()
+    reqs = S.graphene_requests(rate=300.0, duration=0.04, seed=21, sizes=(512, 1024, 2048),
+                               steps_range=(30, 70), check_fraction=0.0)
+    assert len(reqs) >= 6
+    srv = S.Server(1 << 36, steps_per_tick=16, keep_states=True)
+    try:
+        for r in reqs:
+            srv.submit(r)
+        results = srv.run(deadline=300.0)
+    finally:
+        srv.close()
+    assert len(results) == len(reqs) and srv.max_active > 1
+    by_id = {r.rid: r for r in reqs}
+    for res in results:
+        req = by_id[res.rid]
+        assert np.array_equal(res.state, alone(req.make(), req.steps)), res.rid
