@@ -179,8 +179,8 @@ dirac_status dirac_set_scheme(dirac_ctx *ctx, int scheme);
  * They act through the half-step matrix U, which becomes a general complex 2x2 matrix per
  * point, applied by its own pointwise kernel (U before the first pass of a call, U^2
  * between steps, U after the last) instead of inside the line passes. The energy that
- * dirac_observables reports does not include the potentials. Contexts with potentials
- * cannot join a batch. DIRAC_EINVAL for non-finite values. */
+ * dirac_observables reports includes them (H gains V - sum_j a^j A_j sigma_j). Contexts
+ * with potentials cannot join a batch. DIRAC_EINVAL for non-finite values. */
 dirac_status dirac_set_potentials(dirac_ctx *ctx, const double *V, const double *Ax,
                                   const double *Ay);
 

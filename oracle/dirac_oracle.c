@@ -646,7 +646,8 @@ int oracle_run_cn(const oracle_params *p, const double *g00, const double *g11,
  * norm_gamma = hx hy sum w |psi|^2 (eq. l2gamma with the weight sqrt|g| g^00),
  * density = |psi_1|^2 + |psi_2|^2 (Sec. 6.2), and the energy
  * hx hy sum w psi^dagger H psi with H = -i sum_j a^j sigma_j ([[d_j]] + Omega_j)
- * + meff sigma_z (no absorbing layer), reported as real and imaginary parts.
+ * + meff sigma_z (no absorbing layer) + V - sum_j a^j A_j sigma_j (static potentials, when
+ * given), reported as real and imaginary parts.
  * ------------------------------------------------------------------------------- */
 int oracle_observables(const oracle_params *p, const double *g00, const double *g11,
                        const double *g22, const cplx *psi, double *obs, double *density) {
@@ -684,6 +685,19 @@ int oracle_observables(const oracle_params *p, const double *g00, const double *
       /* meff sigma_z psi */
       h1 += me[k] * p1[k];
       h2 += -me[k] * p2[k];
+      /* static potentials: + V psi - a1 Ax sigma_x psi - a2 Ay sigma_y psi */
+      if (p->V) {
+        h1 += p->V[k] * p1[k];
+        h2 += p->V[k] * p2[k];
+      }
+      if (p->Ax) {
+        h1 += -a1[k] * p->Ax[k] * p2[k];
+        h2 += -a1[k] * p->Ax[k] * p1[k];
+      }
+      if (p->Ay) {
+        h1 += -a2[k] * p->Ay[k] * (-I * p2[k]);
+        h2 += -a2[k] * p->Ay[k] * (I * p1[k]);
+      }
       en += w[k] * (conj(p1[k]) * h1 + conj(p2[k]) * h2);
     }
     obs[0] = hx * hy * nrm;

@@ -554,8 +554,10 @@ static dirac_status observables_impl(dirac_ctx* ctx, dirac_obs* out, double* den
   const int blocks = observables_blocks(n);
   CK(launch_observables<T>((const Q4<T>*)ctx->psi, (const Q4<T>*)ctx->scratch1,
                            (const Q4<T>*)ctx->scratch2, ctx->a1, ctx->a2, ctx->meff, ctx->w,
-                           ctx->omx, ctx->omy, n, density_host ? ctx->density : nullptr,
-                           ctx->partials, blocks, st),
+                           ctx->omx, ctx->omy, ctx->pot_use[0] ? ctx->pot_v : nullptr,
+                           ctx->pot_use[1] ? ctx->pot_ax : nullptr,
+                           ctx->pot_use[2] ? ctx->pot_ay : nullptr, n,
+                           density_host ? ctx->density : nullptr, ctx->partials, blocks, st),
      "observables");
   const double hxhy = (2.0 * ctx->ax / ctx->nx) * (2.0 * ctx->ay / ctx->ny);
   CK(launch_reduce_partials(ctx->partials, blocks, hxhy, ctx->result, st), "reduce");

@@ -123,11 +123,13 @@ cudaError_t launch_pack(const double* src, Q4<T>* psi, size_t n, cudaStream_t st
 template <typename T>
 cudaError_t launch_unpack(const Q4<T>* psi, double* dst, size_t n, cudaStream_t st);
 // Per-block FP64 partial sums {norm, norm_gamma, e_re, e_im} into partials[blocks][4]
-// and the density map (if not null). dx and dy may be null (no energy).
+// and the density map (if not null). dx and dy may be null (no energy); the static
+// potentials V, Ax, Ay may be null (0).
 template <typename T>
 cudaError_t launch_observables(const Q4<T>* psi, const Q4<T>* dx, const Q4<T>* dy,
                                const double* a1, const double* a2, const double* meff,
                                const double* w, const double* omx, const double* omy,
+                               const double* V, const double* Ax, const double* Ay,
                                size_t n, double* density, double* partials, int blocks,
                                cudaStream_t st);
 cudaError_t launch_reduce_partials(const double* partials, int blocks, double scale,

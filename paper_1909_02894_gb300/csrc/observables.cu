@@ -71,8 +71,9 @@ __device__ inline void block_sum4(double (&v)[4], double* out) {
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_observables(
     const Q4<T>* psi, const Q4<T>* dx, const Q4<T>* dy, const double* a1, const double* a2,
-    const double* meff, const double* w, const double* omx, const double* omy, size_t n,
-    double* density, double* partials) {
+    const double* meff, const double* w, const double* omx, const double* omy,
+    const double* V, const double* Ax, const double* Ay, size_t n, double* density,
+    double* partials) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (size_t)gridDim.x * blockDim.x) {
@@ -92,10 +93,16 @@ __global__ void __launch_bounds__(TPB) k_observables(
       const double fy1r = gy.x + oy * p1r, fy1i = gy.y + oy * p1i;
       const double fy2r = gy.z + oy * p2r, fy2i = gy.w + oy * p2i;
       // h1 = -i a1 phx2 - a2 phy2 + me p1 ; h2 = -i a1 phx1 + a2 phy1 - me p2
-      const double h1r = A1 * fx2i - A2 * fy2r + me * p1r;
-      const double h1i = -A1 * fx2r - A2 * fy2i + me * p1i;
-      const double h2r = A1 * fx1i + A2 * fy1r - me * p2r;
-      const double h2i = -A1 * fx1r + A2 * fy1i - me * p2i;
+      double h1r = A1 * fx2i - A2 * fy2r + me * p1r;
+      double h1i = -A1 * fx2r - A2 * fy2i + me * p1i;
+      double h2r = A1 * fx1i + A2 * fy1r - me * p2r;
+      double h2i = -A1 * fx1r + A2 * fy1i - me * p2i;
+      // static potentials: + V psi - (a1 Ax sigma_x + a2 Ay sigma_y) psi
+      const double vk = V ? V[k] : 0.0, xk = Ax ? A1 * Ax[k] : 0.0, yk = Ay ? A2 * Ay[k] : 0.0;
+      h1r += vk * p1r - xk * p2r - yk * p2i;
+      h1i += vk * p1i - xk * p2i + yk * p2r;
+      h2r += vk * p2r - xk * p1r + yk * p1i;
+      h2i += vk * p2i - xk * p1i - yk * p1r;
       // conj(p1) h1 + conj(p2) h2
       acc[2] += wk * (p1r * h1r + p1i * h1i + p2r * h2r + p2i * h2i);
       acc[3] += wk * (p1r * h1i - p1i * h1r + p2r * h2i - p2i * h2r);
@@ -108,10 +115,11 @@ template <typename T>
 cudaError_t launch_observables(const Q4<T>* psi, const Q4<T>* dx, const Q4<T>* dy,
                                const double* a1, const double* a2, const double* meff,
                                const double* w, const double* omx, const double* omy,
+                               const double* V, const double* Ax, const double* Ay,
                                size_t n, double* density, double* partials, int blocks,
                                cudaStream_t st) {
-  k_observables<T><<<blocks, TPB, 0, st>>>(psi, dx, dy, a1, a2, meff, w, omx, omy, n, density,
-                                           partials);
+  k_observables<T><<<blocks, TPB, 0, st>>>(psi, dx, dy, a1, a2, meff, w, omx, omy, V, Ax, Ay,
+                                           n, density, partials);
   return cudaGetLastError();
 }
 
@@ -137,6 +145,7 @@ cudaError_t launch_reduce_partials(const double* partials, int blocks, double sc
   template cudaError_t launch_pack<T>(const double*, Q4<T>*, size_t, cudaStream_t);          \
   template cudaError_t launch_unpack<T>(const Q4<T>*, double*, size_t, cudaStream_t);        \
   template cudaError_t launch_observables<T>(const Q4<T>*, const Q4<T>*, const Q4<T>*,       \
+                                             const double*, const double*, const double*,    \
                                              const double*, const double*, const double*,    \
                                              const double*, const double*, const double*,    \
                                              size_t, double*, double*, int, cudaStream_t);

@@ -109,3 +109,18 @@ def test_potentials_can_be_removed_and_batches_refuse_them():
         assert W.rel_l2(s.get_state(), ref) <= 1e-11
         with pytest.raises(D.DiracError):
             D.dirac_set_potentials(s.ctx, np.full((w.ny, w.nx), np.nan), None, None)
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PID)
+def test_energy_with_potentials_matches_oracle(prec):
+    w = W.graphene_strained(n=128, steps=10)
+    w.mass = 0.3
+    psi = w.psi0 + 0.05 * W.random_state(w.nx, w.ny, 8)
+    ref = oracle.observables(oracle_problem(w), psi)
+    with D.Simulation(w, precision=prec) as s:
+        D.dirac_set_potentials(s.ctx, *fields(w))
+        s.set_state(psi)
+        got = s.observables()
+    tol = 1e-11 if prec == D.DIRAC_C128 else 1e-5
+    for k in ("norm", "norm_gamma", "energy"):
+        assert abs(got[k] - ref[k]) <= tol * abs(ref[k]), (k, got[k], ref[k])

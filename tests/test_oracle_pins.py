@@ -857,3 +857,23 @@ def test_potentials_brute_force_dense_step(oracle_lib):
         v[e] = 1.0
         got = oracle_lib.run(prob, v.reshape(2, ny, nx), dt, 1).ravel()
         assert np.abs(got - ref[:, e]).max() <= 1e-12
+
+
+def test_energy_with_potentials_flat_parseval(oracle_lib):
+    """Flat space, constant potentials: the energy is sum_p psi_p^dagger H(xi_p) psi_p
+    h^2/N^2 with H(xi) = sigma.(xi - A) + m sigma_z + V (Parseval)."""
+    n, a, mass, V, Ax, Ay = 32, 5.0, 0.6, 0.35, 0.4, -0.7
+    psi = W.random_state(n, n, 4)
+    prob = problem(oracle_lib, n, n, a, a, mass=mass)
+    prob.V, prob.Ax, prob.Ay = (np.full((n, n), v) for v in (V, Ax, Ay))
+    obs = oracle_lib.observables(prob, psi)
+    xs = xi_vec(n, a)
+    KX, KY = np.meshgrid(xs, xs, indexing="xy")
+    h0, h1 = np.fft.fft2(psi[0]), np.fft.fft2(psi[1])
+    qx, qy = KX - Ax, KY - Ay
+    Hh0 = (mass + V) * h0 + (qx - 1j * qy) * h1
+    Hh1 = (qx + 1j * qy) * h0 + (V - mass) * h1
+    h = 2 * a / n
+    ref = (np.vdot(h0, Hh0) + np.vdot(h1, Hh1)) * h * h / n ** 2
+    assert abs(obs["energy"] - ref.real) <= 1e-12 * abs(ref)
+    assert abs(obs["energy_imag"]) <= 1e-12 * abs(ref)
