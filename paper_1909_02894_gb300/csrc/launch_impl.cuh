@@ -97,7 +97,7 @@ static int sm_count() {
 }
 
 // Persistent prefetching variant (complex64 step mode, 256..4096-point lines): one
-// 1024-thread CTA per SM (clusters of 4 / LPI CTAs for 2048- and 4096-point lines), as
+// 1024-thread CTA per SM (clusters of 2 for 4096-point lines), as
 // many as can be resident, at most one per group of 4096 points.
 template <int L>
 static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st) {

@@ -15,8 +15,8 @@
 // twiddles (cached tables). The FFT, k-space multiply, inverse FFT and epilogue are those
 // of line_pass_kernel (eigencomponent per thread, radix-8 passes). The output leaves in
 // the transposed layout as segments of LPI lines; for 4096-point lines the CTAs run as
-// clusters of 4 that gather their staged lines through distributed shared memory into
-// 4-line segments.
+// clusters of 2 that gather their staged lines through distributed shared memory into
+// 2-line segments.
 //
 // Every wait on an mbarrier is bounded: if one runs out, the CTA records an error code
 // in *err, stops issuing copies and transforming, keeps taking part in the cluster
@@ -33,10 +33,13 @@ struct PGeo {
   static constexpr int THREADS = 1024;
   static constexpr int TPL = 2 * L / E;
   static constexpr int LPI = THREADS / TPL;  // lines per group
-  // CTAs per cluster: 4 for 4096-point lines (64-B output segments measured faster than
-  // 16-B ones); shorter lines write LPI-line segments without a cluster (the cluster
-  // barriers cost more than they saved at 2048 points).
-  static constexpr int CS = L == 4096 ? 4 : 1;
+  // CTAs per cluster: 2 for 4096-point lines, whose output then leaves in 32-byte
+  // (one DRAM sector) segments of 2 lines. Clusters of 2 keep every SM busy (76 x 2 CTAs
+  // resident on 152 SMs; clusters of 4 fit only 36 x 4) and measured faster than both
+  // clusters of 4 (64-B segments) and no cluster (16-B segments). Shorter lines write
+  // LPI-line segments without a cluster (the cluster barriers cost more than they saved at
+  // 2048 points).
+  static constexpr int CS = L == 4096 ? 2 : 1;
   static constexpr int GL = LPI * CS;               // lines per output segment
   using G = Geo<T, L, LPI, E>;               // FFT buffer plan (padded, conflict-free)
   // 4096-point lines run the digit-swap FFT (fft4096_swap): unpadded component buffers,
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
           const int itm = tid + q * PG::THREADS;
-          val[q] = stage[(size_t)(itm % GL) * (L + 1) + i0 + itm / GL];
+          val[q] = stage[(size_t)(itm % GL) * (L + 1) + PG::spos(i0 + itm / GL)];
         }
       }
 #pragma unroll
