@@ -216,6 +216,13 @@ __device__ __forceinline__ void tmem_wait_ld() {
 }
 // Cluster barrier without release semantics: orders execution only (no wait for this
 // thread's outstanding global stores); the wait side keeps acquire.
+// split cluster barrier: arrive without release semantics, and the matching wait
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void cluster_sync_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" :::
                    "memory");

@@ -159,7 +159,7 @@ __device__ __forceinline__ void tmem_swap(Cx<T> (&v)[8], uint32_t x, int s, int 
 template <typename T, bool INV>
 __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, int j, int s,
                                              int q, uint32_t tws, uint32_t x,
-                                             const Cx<T>* t3) {
+                                             const Cx<T>* t3, bool wait_cluster = false) {
   {
     float t1[16];
     tmem_ld16(tws, t1);
@@ -186,8 +186,10 @@ __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, i
   const int rbase = (lo * 512 + mid * 64 + hi) ^ (m & 7);
   const int m3 = (m >> 3) & 1;  // flips bit 3, the low bit of r's field
   const int rb0 = rbase + 8 * m3, rb1 = rbase - 8 * m3;
-  // earlier readers of the buffer finished before a barrier the caller has passed: the
-  // previous group's gather (cluster barrier) or the forward FFT (barrier between FFTs)
+  // Earlier readers of the buffer have finished: the previous group's gather (the wait of
+  // the split cluster barrier, here when wait_cluster is set, or a barrier the caller
+  // passed) or the forward FFT (the barrier between the transforms).
+  if (wait_cluster) cluster_wait();
 #pragma unroll
   for (int r = 0; r < 8; ++r) fc[(r & 1 ? wb1 : wb0) + 64 * r] = v[r];
   __syncthreads();
@@ -336,6 +338,11 @@ __global__ void __launch_bounds__(1024, 1)
   uint32_t issued[2] = {first_issue, first_issue};
   uint32_t done[2] = {0u, 0u};
   int it = 0;
+  // clusters: the barrier after the transposed store is split; its arrive ends an
+  // iteration and its wait comes just before the next write into the staging area (the
+  // forward FFT's shared-memory exchange), so the load and the first FFT passes overlap
+  // the peer's gather. pend: an arrive awaits its wait (uniform across the cluster)
+  bool pend = false;
   for (int s = cluster_id; s < n_super; s += n_clusters, ++it) {
     const uint32_t par = (uint32_t)it & 1u;
     const int g = s * CS + rank;
@@ -406,11 +413,12 @@ __global__ void __launch_bounds__(1024, 1)
       }
     }
     if (!failed) {
-      if constexpr (PG::SWAP)
+      if constexpr (PG::SWAP) {
         fft4096_swap<T, false>(v, fbuf + c * L, 9 * c, j, slice, quarter,
                                tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
-                               t3tab + 8 * slice);
-      else
+                               t3tab + 8 * slice, CS > 1 && pend);
+        pend = false;
+      } else
         fft_passes<T, L, E, false>(v, buf, j, a.tw);
 #pragma unroll
       for (int m = 0; m < E; ++m) {
@@ -499,6 +507,12 @@ __global__ void __launch_bounds__(1024, 1)
         }
       }
     }
+    if constexpr (CS > 1) {
+      if (pend) {  // no forward FFT ran in this iteration (failure)
+        cluster_wait();
+        pend = false;
+      }
+    }
     // ---- transposed store of the super-group: out[i][s GL .. s GL + GL); CTA rank q
     // writes rows i of its L/CS slice, reading the owners' staging buffers. The barrier
     // publishes the staging writes and tells thread 0 that the b - 1 / U zone is free.
@@ -550,7 +564,16 @@ __global__ void __launch_bounds__(1024, 1)
     // the staging buffer is free for the next super-group once every CTA of the cluster
     // has read it (the loads have returned: the stores above consumed them), so the
     // arrive needs no release fence for the outstanding global stores
-    if constexpr (CS > 1) cluster_sync_relaxed(); else __syncthreads();
+    if constexpr (CS > 1) {
+      cluster_arrive_relaxed();
+      pend = true;
+    } else {
+      __syncthreads();
+    }
+  }
+  if constexpr (CS > 1) {
+    // the peer may still be reading this CTA's staged lines
+    if (pend) cluster_wait();
   }
   if (failed && tid == 0) {
     // at most one copy per mbarrier is outstanding: the last one requested

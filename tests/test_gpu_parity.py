@@ -235,6 +235,25 @@ def test_autotune_keeps_state_and_picks_a_valid_shape(prec, tmp_path):
         assert autotune.tune(s, prec, cache_path=str(tmp_path / "cache.json")) == (tx, ty)
 
 
+def test_bounded_wait_timeout_in_the_clustered_4096_pass():
+    """The same on the 4096^2 complex64 grid: the persistent 4096-point pass runs as
+    clusters whose CTAs keep taking part in the cluster barriers after a wait has run out,
+    so every CTA returns; the context works again afterwards."""
+    w = W.large_4096(steps=1)
+    with D.Simulation(w, precision=D.DIRAC_C64) as s:
+        s.set_state(w.psi0)
+        D.dirac_test_timeout_next_step(s.ctx)
+        s.step(1, w.dt)
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_synchronize(s.ctx)
+        assert e.value.status == D.DIRAC_ETIMEOUT
+        s.set_state(w.psi0)
+        s.step(1, w.dt)
+        got = s.get_state()
+    ref = oracle_run(w, 1)
+    assert W.rel_l2(got, ref) <= TOL[D.DIRAC_C64]
+
+
 def test_bounded_wait_timeout_is_reported_and_context_recovers():
     """Failure detection without a GPU fault: a bulk-copy wait that nothing completes
     runs out after its bound; the kernel returns, dirac_synchronize reports
