@@ -246,9 +246,12 @@ struct Geo {
   static constexpr int CM = SmemPlan<T, L, E>::CM;
   static constexpr int COMP = P + (((CM - P % B) % B) + B) % B;
   static constexpr int STRIDE = 2 * COMP + SmemPlan<T, L, E>::EXTRA;
-  // Lines gathered per output segment: 4 (64 B complex64, 128 B complex128). A cluster of
-  // 4 CTAs packs the GPCs better than 8 and measured faster at 1024..4096 points.
-  static constexpr int G = 4;
+  // Lines gathered per output segment: 4 (64 B complex64, 128 B complex128), 2 for
+  // 4096-point lines. A cluster of 4 CTAs packs the GPCs better than 8 and measured faster
+  // at 1024..2048 points; 4096-point lines run one CTA per SM, where only 36 clusters of 4
+  // (144 CTAs) but 76 clusters of 2 (every SM) are resident: clusters of 2 measured 6-7%
+  // faster at 4096^2 in both precisions.
+  static constexpr int G = L == 4096 ? 2 : 4;
   static constexpr int CS = LPC >= G ? 1 : G / LPC;   // CTAs per cluster
   static constexpr int GL = LPC * CS;                  // lines gathered per output segment
   static constexpr int LOG2L = ilog2c(L);
