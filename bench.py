@@ -7,7 +7,7 @@ strain bumps, absorbing layer 128, dt=0.05), whose state and coefficient fields 
 larger than L2, so no flush is needed between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--workload large-4096|graphene-1024-c64|graphene-1024-c128|plain-128-c128]
+                    [--workload large-4096|large-2048|graphene-1024-c64|graphene-1024-c128|plain-128-c128]
 
 Prints one JSON line. The path does not shard: with N > 1 each rank runs an
 independent replica and `value` sums the ranks ("replicas only", weak scaling).
@@ -40,6 +40,8 @@ def workload(name):
     """(Workload, precision name, algorithmic bytes per grid point per step)."""
     if name == "large-4096":
         return W.large_4096(), "c64", 88
+    if name == "large-2048":
+        return W.large_4096(n=2048), "c64", 88
     if name == "graphene-1024-c64":
         return W.graphene_strained(n=1024), "c64", 88
     if name == "graphene-1024-c128":
@@ -164,6 +166,7 @@ def run_reference(args, wl_name):
     oracle.build()
     w_full, prec, _ = workload(wl_name)
     recipe = {"large-4096": lambda n: W.large_4096(n=n, steps=1),
+              "large-2048": lambda n: W.large_4096(n=n, steps=1),
               "graphene-1024-c64": lambda n: W.graphene_strained(n=n, steps=1),
               "graphene-1024-c128": lambda n: W.graphene_strained(n=n, steps=1),
               "plain-128-c128": lambda n: W.plain_128(n=n, steps=1)}[wl_name]
