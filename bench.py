@@ -153,6 +153,25 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(ms, world, device=None):
+    """The slowest rank's time: all_reduce(MAX) over the process group (NCCL with CUDA
+    tensors, gloo with CPU ones); a single process returns its own."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(points_per_rank, steps, world, ms):
+    """Grid-point steps per second of the whole job: every rank runs an independent
+    replica of `points_per_rank` points for `steps` steps, over the slowest rank's time."""
+    return points_per_rank * steps * world / (ms * 1e-3)
+
+
 def run_reference(args, wl_name):
     """The FP64 CPU oracle, as it stands, timed on the host cores as the reference arm.
     Each of the K timed steps is one oracle time step on a bounded sample of the
@@ -238,6 +257,8 @@ def run_batch(args):
 
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
+    if world > 1:  # independent replicas of the whole mix, one per rank
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     count = args.batch_count
     ws = W.batch_mix(count=count, steps=args.steps)
     stream = torch.cuda.Stream()
@@ -253,6 +274,8 @@ def run_batch(args):
             s.set_state(w.psi0)
             slots.append(D.dirac_batch_submit(batch, s.ctx, n_steps, w.dt))
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -263,13 +286,13 @@ def run_batch(args):
         torch.cuda.synchronize()
         for sl in slots:
             D.dirac_batch_release(batch, sl)
-        return e0.elapsed_time(e1)
+        return max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
 
     run(max(3, args.warmup))
     l0 = D.dirac_batch_launch_count(batch)
     with Clocks(local) as clk:
         ms = run(args.steps)
-    value = pts * args.steps / (ms * 1e-3)
+    value = whole_job_value(pts, args.steps, world, ms)
     # plain complex128 path, each instance alone, on a bounded sample (one of each size)
     sample, seen = [], set()
     for w in ws:
@@ -303,7 +326,7 @@ def run_batch(args):
         "plain_c128_single_instance": {"value": plain, "unit": UNIT,
                                        "sample": f"one instance of each size, {plain_steps} steps, "
                                                  "scaled by the mix's point counts"},
-        "batched_over_plain_c128": value / plain,
+        "batched_over_plain_c128": value / world / plain,
         "clocks": clk.summary(),
         "gpu_launches": int(D.dirac_batch_launch_count(batch) - l0),
     }
@@ -312,6 +335,8 @@ def run_batch(args):
     D.dirac_batch_destroy(batch)
     for s in sims:
         s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -326,6 +351,8 @@ def run_serve(args):
     from paper_1909_02894_gb300 import serve as S
 
     world, rank, local = dist_setup(args)
+    if rank != 0:  # one request stream, served by rank 0's GPU; other ranks have no work
+        return 0
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     free, total = torch.cuda.mem_get_info()
@@ -358,7 +385,7 @@ def run_serve(args):
         out[label] = summ
     line = {
         "metric": "p50/p99 solve ms and grid-point*steps/s (serving)",
-        "value": out["configured"]["throughput"], "unit": UNIT, "n_gpus": world,
+        "value": out["configured"]["throughput"], "unit": UNIT, "n_gpus": 1,
         "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve-graphene", "arrivals": "Poisson",
@@ -457,12 +484,8 @@ def main():
         ev1.record(stream)
         barrier()
     launches = D.dirac_launch_count(sim.ctx) - l0
-    ms = ev0.elapsed_time(ev1)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
-    value = pts * args.steps * world / (ms * 1e-3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, device="cuda")
+    value = whole_job_value(pts, args.steps, world, ms)
 
     # ---- roofline of the dominant kernel (the fused line pass, 2 launches per step, 3 in
     # the symmetric order; the timed region holds nothing else, so its average launch
@@ -498,8 +521,9 @@ def main():
             sim.step(solve_steps, w.dt)
             D.lib().dirac_get_state(sim.ctx, host_out.data_ptr(), 0)
         barrier()
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": pts * solve_steps * args.e2e_solves * world / t_e2e, "unit": UNIT,
+        ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3, world, device="cuda")
+        e2e = {"value": whole_job_value(pts, solve_steps * args.e2e_solves, world, ms_e2e),
+               "unit": UNIT,
                "h2d_bytes_per_step": host_in.numel() * 16,
                "d2h_bytes_per_step": host_out.numel() * 16,
                "step": f"one solve: set_state(host) + {solve_steps} steps + get_state(host)"}
