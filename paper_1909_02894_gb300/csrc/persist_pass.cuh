@@ -414,9 +414,13 @@ __global__ void __launch_bounds__(1024, 1)
     }
     if (!failed) {
       if constexpr (PG::SWAP) {
+        // batched launches wait before the transform: inside it, the extra branch makes
+        // the compiler spill the instance's pointers
+        if constexpr (BATCH && CS > 1)
+          if (pend) cluster_wait();
         fft4096_swap<T, false>(v, fbuf + c * L, 9 * c, j, slice, quarter,
                                tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
-                               t3tab + 8 * slice, CS > 1 && pend);
+                               t3tab + 8 * slice, !BATCH && CS > 1 && pend);
         pend = false;
       } else
         fft_passes<T, L, E, false>(v, buf, j, a.tw);
