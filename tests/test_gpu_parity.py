@@ -187,6 +187,47 @@ def test_step_before_state_and_nonfinite_state():
         assert e.value.status == D.DIRAC_ENONFINITE
 
 
+@pytest.mark.parametrize("prec", PREC, ids=PID)
+def test_zero_steps_and_invalid_step_arguments(prec):
+    """n_steps = 0 leaves the state bit for bit; negative n_steps and dt <= 0, NaN or inf
+    are refused with DIRAC_EINVAL before any device work, and the context keeps working."""
+    w = W.plain_128(n=64)
+    with D.Simulation(w, precision=prec) as s:
+        s.set_state(w.psi0)
+        before = s.get_state()
+        s.step(0, w.dt)
+        assert np.array_equal(s.get_state(), before)
+        for n, dt in ((-1, w.dt), (1, 0.0), (1, -w.dt), (1, float("nan")), (1, float("inf"))):
+            with pytest.raises(D.DiracError) as e:
+                s.step(n, dt)
+            assert e.value.status == D.DIRAC_EINVAL
+        assert np.array_equal(s.get_state(), before)
+        s.step(5, w.dt)
+        got = s.get_state()
+    assert W.rel_l2(got, oracle_run(w, 5)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PREC, ids=PID)
+@pytest.mark.parametrize("scheme", [D.DIRAC_SCHEME_II, D.DIRAC_SCHEME_II_SYMMETRIC],
+                         ids=["printed", "symmetric"])
+def test_dt_change_between_calls(prec, scheme):
+    """A call with another dt rebuilds the half steps and k-space tables: 7 steps of dt
+    then 5 of dt / 2 give the oracle's 7 + 5 steps (the U of the first call's last half
+    step and the second call's first are those of their own dt)."""
+    w = W.graphene_strained(n=128, steps=12)
+    w.mass = 0.3
+    prob = oracle.Problem.from_workload(w)
+    osch = oracle.SCHEME_II if scheme == D.DIRAC_SCHEME_II else oracle.SCHEME_II_SYMMETRIC
+    ref = oracle.run(prob, w.psi0, w.dt, 7, scheme=osch)
+    ref = oracle.run(prob, ref, 0.5 * w.dt, 5, scheme=osch)
+    with D.Simulation(w, precision=prec, scheme=scheme) as s:
+        s.set_state(w.psi0)
+        s.step(7, w.dt)
+        s.step(5, 0.5 * w.dt)
+        got = s.get_state()
+    assert W.rel_l2(got, ref) <= TOL[prec]
+
+
 def test_norm_conserved_in_flat_space_on_gpu():
     w = W.plain_128(flat=True)
     w.mass = 0.5
