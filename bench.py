@@ -71,6 +71,18 @@ def hbm_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# FP64 rate of GB300 (nominal 1.25 TFLOP/s dense FP64: 2 FP64 FMAs per SM per clock on 152
+# SMs at 2.07 GHz); the complex128 line pass is bound by it, not by HBM.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fft_flops_per_point_step(nx, ny):
+    """Algorithmic flops of one Scheme II step per grid point, by the 5 N log2 N convention
+    for a complex FFT of N points: per direction two components, forward and inverse
+    (4 x 5 log2 N per point), plus about 76 pointwise flops (k-space multiply, combine, U)."""
+    return 20.0 * (np.log2(nx) + np.log2(ny)) + 76.0
+
+
 def kernel_hash():
     h = hashlib.sha256()
     for f in ("line_pass.cuh", "persist_pass.cuh", "launch_impl.cuh", "common.cuh"):
@@ -528,6 +540,21 @@ def main():
                "d2h_bytes_per_step": host_out.numel() * 16,
                "step": f"one solve: set_state(host) + {solve_steps} steps + get_state(host)"}
 
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "whole step (derivative passes, transposes, combines)"
+                if (poly or cn) else kernel_name(w, prec_name),
+                "algorithmic_bytes_per_point_step": bytes_pt}
+    if prec == D.DIRAC_C128 and not (poly or cn):
+        # FP64-bound: algorithmic flops per launch over the average launch duration
+        fl_pt = fft_flops_per_point_step(w.nx, w.ny)
+        tflops = fl_pt * pts / float(passes) / per_launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "nominal FP64 (2 FMA per SM per clock, 152 SMs, 2.07 GHz)",
+                    "kernel": kernel_name(w, prec_name),
+                    "algorithmic_flops_per_point_step": fl_pt,
+                    "hbm_frac": achieved / peak}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -544,12 +571,7 @@ def main():
                        "dt": w.dt, "absorber": w.pml_width_x, "parallelism": "replicas",
                        "l2": "inputs larger than L2 (no flush)"
                        if bytes_pt * pts > L2_BYTES else "working set fits L2"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_source": peak_kind,
-                         "kernel": "whole step (derivative passes, transposes, combines)"
-                         if (poly or cn) else kernel_name(w, prec_name),
-                         "algorithmic_bytes_per_point_step": bytes_pt},
+            "roofline": roofline,
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
             "e2e": e2e,
