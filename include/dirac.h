@@ -200,12 +200,15 @@ dirac_status dirac_set_krylov(dirac_ctx *ctx, double tol, int restart, int max_r
 long dirac_krylov_iterations(const dirac_ctx *ctx);
 
 /* CTA shape of the two fused passes (each pass: FFT along a line, k-space multiply,
- * inverse FFT, combine, transposed store): about 256 or 512 threads per CTA for that
- * pass's line length, or 1024 for the persistent prefetching variant (complex64, lines
- * of 256..4096 points; one CTA per SM streams the next lines into shared memory while
- * it transforms the current ones); 0 = the default (persistent for complex64 lines of
- * 1024 points or more, else 512). Lines of 128 points or fewer have one shape only.
- * Used by the autotuner. DIRAC_EINVAL for other values. */
+ * inverse FFT, combine, transposed store): 256 selects the smaller and 512 the larger of
+ * the pass's two shapes for its line length (complex64: about 256 and 512 threads per
+ * CTA; complex128: 1 to 4 lines per CTA, 32 to 512 threads), 1024 the persistent
+ * prefetching variant (complex64, lines of 256..4096 points; one CTA per SM streams the
+ * next lines into shared memory while it transforms the current ones); 0 = the default
+ * (complex64: persistent for lines of 1024 points or more, else the larger shape;
+ * complex128: the smaller shape for 1024-point lines, else the larger). Lines of 128
+ * points or fewer and 4096-point lines have one shape only. Used by the autotuner.
+ * DIRAC_EINVAL for other values. */
 dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_pass);
 
 /* Autotuner: times every CTA shape of the x and the y pass (reps launches each, CUDA

@@ -63,8 +63,11 @@ static int pass_opt(const dirac_ctx* ctx, int threads, int L) {
   if (threads == 256) return 0;
   if (threads == 512) return 1;
   if (threads == 1024) return 2;
-  // default: the persistent prefetching pass for long complex64 lines
-  return (ctx->prec == DIRAC_C64 && L >= 1024) ? 2 : 1;
+  // default: the persistent prefetching pass for long complex64 lines; in complex128 the
+  // smaller shape for 1024-point lines (one line per CTA: 1024 CTAs spread over the SMs to
+  // within one line, 0.74 against 0.89 ms per 1024^2 step), else the larger
+  if (ctx->prec == DIRAC_C64) return L >= 1024 ? 2 : 1;
+  return L == 1024 ? 0 : 1;
 }
 
 // Reads and clears the device error flag (after the stream has been synchronised).

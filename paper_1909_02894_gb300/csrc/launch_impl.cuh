@@ -54,7 +54,12 @@ static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
 // fewer and 4096-point lines have one). Lines per CTA, by precision:
 //   FP32 (E = 8 from 256 points): 256: 4|8, 512: 2|4, 1024: 1|2, 2048: 1|2, 4096: 1
 //     (256|512 threads, 512|1024 at 2048, 1024 at 4096)
-//   FP64 (E = 16): 256: 8|16, 512: 4|8, 1024: 2|4, 2048: 1|2, 4096: 1 (256|512 threads)
+//   FP64 (E = 16): 256: 1|2, 512: 2|4, 1024: 1|2, 2048: 1|2, 4096: 1 (32..512 threads).
+//     The FP64 pass is bound by the FP64 units and its CTAs hold 128-162 registers per
+//     thread, so few CTAs fit an SM: small CTAs keep all 152 SMs evenly loaded. Measured on
+//     the strained-graphene grids (ms per step, opt 0 | opt 1): 256^2 0.096 | 0.096,
+//     512^2 0.203 | 0.199, 1024^2 0.741 | 0.886, 2048^2 3.61 | 3.20; the shapes used before
+//     (256: 8|16, 512: 4|8, 1024: 2|4) took 0.180 | 0.350, 0.199 | 0.387, 0.885 | 0.832.
 //   both: 16 lines per CTA up to 128 points.
 template <typename T, int MODE>
 static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) {
@@ -71,18 +76,18 @@ static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) 
   if constexpr (MODE == MODE_STEP) {
     if (big) {
       switch (a.L) {
-        case 256: return launch_one<T, 256, F ? 8 : 16, MODE>(a, st);
-        case 512: return launch_one<T, 512, F ? 4 : 8, MODE>(a, st);
-        case 1024: return launch_one<T, 1024, F ? 2 : 4, MODE>(a, st);
+        case 256: return launch_one<T, 256, F ? 8 : 2, MODE>(a, st);
+        case 512: return launch_one<T, 512, 4, MODE>(a, st);
+        case 1024: return launch_one<T, 1024, 2, MODE>(a, st);
         case 2048: return launch_one<T, 2048, 2, MODE>(a, st);
         default: return cudaErrorInvalidValue;
       }
     }
   }
   switch (a.L) {
-    case 256: return launch_one<T, 256, F ? 4 : 8, MODE>(a, st);
-    case 512: return launch_one<T, 512, F ? 2 : 4, MODE>(a, st);
-    case 1024: return launch_one<T, 1024, F ? 1 : 2, MODE>(a, st);
+    case 256: return launch_one<T, 256, F ? 4 : 1, MODE>(a, st);
+    case 512: return launch_one<T, 512, 2, MODE>(a, st);
+    case 1024: return launch_one<T, 1024, 1, MODE>(a, st);
     case 2048: return launch_one<T, 2048, 1, MODE>(a, st);
     default: return cudaErrorInvalidValue;
   }
