@@ -205,7 +205,8 @@ long dirac_krylov_iterations(const dirac_ctx *ctx);
  * CTA; complex128: 1 to 4 lines per CTA, 32 to 512 threads), 1024 the persistent
  * prefetching variant (complex64, lines of 256..4096 points; one CTA per SM streams the
  * next lines into shared memory while it transforms the current ones); 0 = the default
- * (complex64: persistent for lines of 1024 points or more, else the larger shape;
+ * (complex64: persistent for lines of 1024 points or more, the smaller shape for
+ * 256-point lines, else the larger;
  * complex128: the smaller shape for 1024-point lines, else the larger). Lines of 128
  * points or fewer and 4096-point lines have one shape only. Used by the autotuner.
  * DIRAC_EINVAL for other values. */

@@ -63,10 +63,12 @@ static int pass_opt(const dirac_ctx* ctx, int threads, int L) {
   if (threads == 256) return 0;
   if (threads == 512) return 1;
   if (threads == 1024) return 2;
-  // default: the persistent prefetching pass for long complex64 lines; in complex128 the
-  // smaller shape for 1024-point lines (one line per CTA: 1024 CTAs spread over the SMs to
-  // within one line, 0.74 against 0.89 ms per 1024^2 step), else the larger
-  if (ctx->prec == DIRAC_C64) return L >= 1024 ? 2 : 1;
+  // Default, by measurement on the strained-graphene grids: complex64 the persistent
+  // prefetching pass for lines of 1024 points or more, the smaller shape for 256-point
+  // lines (0.016 against 0.018 ms per 256^2 step), else the larger; complex128 the smaller
+  // shape for 1024-point lines (one line per CTA: 1024 CTAs spread over the SMs to within
+  // one line, 0.74 against 0.89 ms per 1024^2 step), else the larger.
+  if (ctx->prec == DIRAC_C64) return L >= 1024 ? 2 : L == 256 ? 0 : 1;
   return L == 1024 ? 0 : 1;
 }
 
