@@ -327,6 +327,14 @@ def run_batch(args):
             t_plain += e0.elapsed_time(e1) * 1e-3 / plain_steps * sum(
                 x.points for x in ws if x.nx == w.nx) / w.points
     plain = pts / t_plain
+    # the whole tick against HBM: every instance's step moves the same 88 B per point as a
+    # single grid's (all classes' launches, per replica)
+    peak, peak_kind = hbm_peak()
+    gbs = 88.0 * pts / (ms * 1e-3 / args.steps) / 1e9
+    batch_roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                      "frac": gbs / peak, "traffic": None, "peak_source": peak_kind,
+                      "kernel": "whole tick (every class's x and y passes)",
+                      "algorithmic_bytes_per_point_step": 88}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -339,6 +347,7 @@ def run_batch(args):
                                        "sample": f"one instance of each size, {plain_steps} steps, "
                                                  "scaled by the mix's point counts"},
         "batched_over_plain_c128": value / world / plain,
+        "roofline": batch_roofline,
         "clocks": clk.summary(),
         "gpu_launches": int(D.dirac_batch_launch_count(batch) - l0),
     }
