@@ -16,7 +16,8 @@
 // of line_pass_kernel (eigencomponent per thread, radix-8 passes). The output leaves in
 // the transposed layout as segments of LPI lines; for 4096-point lines the CTAs run as
 // clusters of 2 that gather their staged lines through distributed shared memory into
-// 2-line segments.
+// 2-line segments. 4096- and 1024-point lines run FFTs whose exchanges go through tensor
+// memory (fft4096_swap, fft1024_swap); the other lengths run the Stockham passes.
 //
 // Every wait on an mbarrier is bounded: if one runs out, the CTA records an error code
 // in *err, stops issuing copies and transforming, keeps taking part in the cluster
@@ -45,6 +46,12 @@ struct PGeo {
   // 4096-point lines run the digit-swap FFT (fft4096_swap): unpadded component buffers,
   // which also hold the staging buffer of L + 1 points
   static constexpr bool SWAP = L == 4096;
+  // 1024-point lines run fft1024_swap: line l of the group on the 8 warps of tensor-memory
+  // lane quarter l; warp-local exchange buffers of XQ elements per (component, lane bit 1)
+  // group with rows of XP (conflict free for the 8-byte accesses of both directions)
+  static constexpr bool SWAP1K = L == 1024;
+  static constexpr int XP = 9, XQ = 76;
+  static constexpr size_t XBUF_BYTES = (size_t)(THREADS / 32) * 4 * XQ * sizeof(Cx<T>);
   // The 4096-point path pads its staging buffer and its b - 1 / U zones after every 512
   // points (1 point, 4 floats, 1 matrix), so that the two threads of a point pair, which
   // work on points 512 k apart in the epilogue, reach different banks.
@@ -53,6 +60,8 @@ struct PGeo {
   static constexpr size_t F_RAW =
       SWAP ? ((size_t)2 * L * sizeof(Cx<T>) > STAGE_POINTS * sizeof(Q4<T>)
                   ? (size_t)2 * L * sizeof(Cx<T>) : STAGE_POINTS * sizeof(Q4<T>))
+      : SWAP1K ? (XBUF_BYTES > (size_t)LPI * STAGE_POINTS * sizeof(Q4<T>)
+                      ? XBUF_BYTES : (size_t)LPI * STAGE_POINTS * sizeof(Q4<T>))
            : G::SMEM;
   static constexpr size_t F_BYTES = ((F_RAW + 127) / 128) * 128;
   static constexpr size_t PSI_BYTES = (size_t)LPI * L * sizeof(Q4<T>);
@@ -68,12 +77,14 @@ struct PGeo {
   static constexpr size_t OFF_BAR = OFF_U + CHUNKS * U_PITCH;
   static constexpr size_t OFF_T3 = OFF_BAR + 32;  // two mbarriers + tensor-memory address
   // pass-3 twiddles of the digit-swap FFT: 8 warp slices x 8 entries (the 7 powers, a pad)
-  static constexpr size_t SMEM = OFF_T3 + 64 * sizeof(Cx<T>);
+  static constexpr size_t OFF_T2 = OFF_T3 + 64 * sizeof(Cx<T>);
+  // W_128^(u t) (t = 1..7 rows of 16) of the 1024-point FFT
+  static constexpr size_t SMEM = OFF_T2 + (SWAP1K ? 128 : 0) * sizeof(Cx<T>);
   // tensor memory: 8 warps share each lane quarter; per warp slice s = warp / 4 the
   // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds an
   // exchange region of 128 columns and 32 twiddle columns per slice
-  static constexpr uint32_t T_PARK = 0, T_X = 128, T_TW = 256;
-  static constexpr uint32_t TMEM_COLS = SWAP ? 512 : 128;
+  static constexpr uint32_t T_PARK = 0, T_X = 128, T_TW = 256, T_X2 = 384;
+  static constexpr uint32_t TMEM_COLS = (SWAP || SWAP1K) ? 512 : 128;
   static_assert(sizeof(T) == 4, "persistent pass is complex64 only");
   static_assert(G::THREADS == THREADS, "group must fill the CTA");
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
@@ -211,6 +222,109 @@ __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, i
   dft8<T, INV>(v);
 }
 
+// ---- 1024-point FFT, one line per tensor-memory lane quarter
+//
+// Line l of the group runs on the 8 warps of lane quarter l (warp & 3 == l). Thread
+// (slice s = warp / 4, lane) holds component lane & 1 and of it the elements j + 128 r,
+// r = 0..7, with j = 16 s + u, u = lane / 2 = u0 + 2 u1 (u0 = lane bit 1, u1 = lane bits
+// 2..4). Forward, a decimation in frequency over n = j + 128 b:
+//   DFT-8 over b (registers) -> k0, twiddle W_1024^(j k0);
+//   tensor memory: registers <-> slice (registers s, slice k0);
+//   DFT-8 over s -> k1, twiddle W_128^(u k1);
+//   warp-local exchange through shared memory: registers <-> u1 (lanes k1, registers u1);
+//   DFT-8 over u1 -> v1, twiddle W_16^(u0 v1);
+//   DFT-2 over u0 (lane bit 1, shuffles) -> v0.
+// Element r of thread (s, lane) is then frequency s + 8 (lane >> 2) + 64 r + 512 v0,
+// v0 = (lane >> 1) & 1. The inverse runs the same steps backwards with conjugate twiddles
+// and ends in natural order. Only the tensor-memory exchange synchronises warps (the 8 of
+// the line's quarter); x is the exchange region (one for each direction), xw this warp's
+// exchange buffer, t1 the thread's parked W_1024^(j t), t2 the W_128^(u t) table.
+template <typename T, bool INV>
+__device__ __forceinline__ void tw16_lane(Cx<T> (&v)[8], bool u0) {
+  Cx<T> w[8];
+  w[1] = w16<T, INV, 1>(v[1]);
+  w[2] = w16<T, INV, 2>(v[2]);
+  w[3] = w16<T, INV, 3>(v[3]);
+  w[4] = w16<T, INV, 4>(v[4]);
+  w[5] = w16<T, INV, 4>(w16<T, INV, 1>(v[5]));
+  w[6] = w16<T, INV, 6>(v[6]);
+  w[7] = w16<T, INV, 4>(w16<T, INV, 3>(v[7]));
+#pragma unroll
+  for (int r = 1; r < 8; ++r) v[r] = u0 ? w[r] : v[r];
+}
+
+template <typename T>
+__device__ __forceinline__ void dft2_lane(Cx<T> (&v)[8], bool hi) {
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const Cx<T> p = {__shfl_xor_sync(0xffffffffu, v[r].re, 2),
+                     __shfl_xor_sync(0xffffffffu, v[r].im, 2)};
+    v[r] = hi ? csub(p, v[r]) : cadd(v[r], p);
+  }
+}
+
+// registers <-> lane bits 2..4 among the 8 lanes of equal lane bits 0..1
+template <typename T, int XP, int XQ>
+__device__ __forceinline__ void warp_xchg(Cx<T> (&v)[8], Cx<T>* xw, int lane) {
+  Cx<T>* g = xw + ((lane & 1) + 2 * ((lane >> 1) & 1)) * XQ;
+  const int l3 = lane >> 2;
+#pragma unroll
+  for (int r = 0; r < 8; ++r) g[l3 * XP + r] = v[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 8; ++r) v[r] = g[r * XP + l3];
+}
+
+template <typename T, bool INV, int XP, int XQ>
+__device__ __forceinline__ void fft1024_swap(Cx<T> (&v)[8], Cx<T>* xw, int lane, int s, int q,
+                                             uint32_t t1, uint32_t x, const Cx<T>* t2) {
+  const bool u0 = (lane >> 1) & 1;
+  const int u = lane >> 1;
+  auto tw128 = [&]() {
+    float f[16];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) {
+      const Cx<T> w = t2[(t - 1) * 16 + u];
+      f[2 * t - 2] = w.re;
+      f[2 * t - 1] = w.im;
+    }
+    f[14] = f[15] = 0.f;
+    twiddle8<T, INV>(v, f);
+  };
+  if constexpr (!INV) {
+    {
+      float f[16];
+      tmem_ld16(t1, f);
+      dft8<T, false>(v);
+      tmem_wait_ld_regs(f);
+      twiddle8<T, false>(v, f);
+    }
+    tmem_swap(v, x, s, q);
+    dft8<T, false>(v);
+    tw128();
+    warp_xchg<T, XP, XQ>(v, xw, lane);
+    dft8<T, false>(v);
+    tw16_lane<T, false>(v, u0);
+    dft2_lane(v, u0);
+  } else {
+    dft2_lane(v, u0);
+    tw16_lane<T, true>(v, u0);
+    dft8<T, true>(v);
+    __syncwarp();  // every lane has read the forward exchange
+    warp_xchg<T, XP, XQ>(v, xw, lane);
+    tw128();
+    dft8<T, true>(v);
+    tmem_swap(v, x, s, q);
+    {
+      float f[16];
+      tmem_ld16(t1, f);
+      tmem_wait_ld_regs(f);
+      twiddle8<T, true>(v, f);
+    }
+    dft8<T, true>(v);
+  }
+}
+
 // BATCH: the launch covers several instances (a0.inst); otherwise every pointer stays a
 // kernel parameter, which the compiler reads from the constant bank instead of keeping
 // in registers. Each instance has at most one of u_load / u_store (the U landing zone
@@ -229,13 +343,17 @@ __global__ void __launch_bounds__(1024, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::OFF_BAR);  // [0] spinor, [1] b-1/U
   uint32_t* tslot = reinterpret_cast<uint32_t*>(psmem + PG::OFF_BAR + 2 * sizeof(uint64_t));
   Cx<T>* t3tab = reinterpret_cast<Cx<T>*>(psmem + PG::OFF_T3);
+  Cx<T>* t2tab = reinterpret_cast<Cx<T>*>(psmem + PG::OFF_T2);
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
-  const int lcta = tid / PG::TPL;
-  const int r = tid - lcta * PG::TPL;
-  const int c = r & 1;
-  const int j = r >> 1;
+  const int lane = tid & 31;
+  Cx<T>* xw = reinterpret_cast<Cx<T>*>(psmem) + (size_t)warp * 4 * PG::XQ;
+  // line within the group, component, and index j of the thread's first element; the
+  // 1024-point FFT puts line l on lane quarter l (warps l, l + 4, ...)
+  const int lcta = PG::SWAP1K ? (warp & 3) : tid / PG::TPL;
+  const int c = PG::SWAP1K ? (lane & 1) : ((tid - lcta * PG::TPL) & 1);
+  const int j = PG::SWAP1K ? 16 * (warp >> 2) + (lane >> 1) : (tid - lcta * PG::TPL) >> 1;
   Cx<T>* buf = fbuf + lcta * Gm::STRIDE + c * Gm::COMP;
   const T sg = c ? T(-1) : T(1);
   constexpr uint32_t GROUP_BYTES = (uint32_t)PG::PSI_BYTES;
@@ -300,6 +418,15 @@ __global__ void __launch_bounds__(1024, 1)
       t3tab[s3 * 8 + t - 1] = ldg_cx(a0.tw + tw_offset(8, 8) + (t - 1) * 8 + s3);
     }
   }
+  if constexpr (PG::SWAP1K) {
+    // W_128^(u t) = W_1024^(8 u t), u < 16, t = 1..7, from the table's W_1024^k, k < 512
+    if (tid < 112) {
+      const int t = tid / 16 + 1, u = tid % 16, e = 8 * u * t;
+      const Cx<T>* w0 = a0.tw + tw_offset(512, 8);
+      const Cx<T> w = ldg_cx(w0 + (e & 511));
+      t2tab[tid] = e < 512 ? w : Cx<T>{-w.re, -w.im};
+    }
+  }
   if (warp == 0) tmem_alloc(tslot, PG::TMEM_COLS);
   tmem_fence_before_sync();
   __syncthreads();
@@ -325,6 +452,21 @@ __global__ void __launch_bounds__(1024, 1)
       f[14] = f[15] = 0.f;
       tmem_st16(tlane + PG::T_TW + 32u * (uint32_t)slice + 16u * (uint32_t)p, f);
     }
+    tmem_wait_st();
+  }
+  if constexpr (PG::SWAP1K) {
+    // W_1024^(j t), t = 1..7, parked once per kernel (W_1024^(k + 512) = -W_1024^k)
+    const Cx<T>* w0 = a0.tw + tw_offset(512, 8);
+    float f[16];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) {
+      const int e = j * t;
+      const Cx<T> w = ldg_cx(w0 + (e & 511));
+      f[2 * t - 2] = e < 512 ? w.re : -w.re;
+      f[2 * t - 1] = e < 512 ? w.im : -w.im;
+    }
+    f[14] = f[15] = 0.f;
+    tmem_st16(tlane + PG::T_TW + 16u * (uint32_t)slice, f);
     tmem_wait_st();
   }
   if (tid == 0 && cluster_id < n_super) {
@@ -422,13 +564,22 @@ __global__ void __launch_bounds__(1024, 1)
                                tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
                                t3tab + 8 * slice, !BATCH && CS > 1 && pend);
         pend = false;
-      } else
+      } else if constexpr (PG::SWAP1K) {
+        fft1024_swap<T, false, PG::XP, PG::XQ>(v, xw, lane, slice, quarter,
+                                               tlane + PG::T_TW + 16u * (uint32_t)slice,
+                                               tlane + PG::T_X, t2tab);
+      } else {
         fft_passes<T, L, E, false>(v, buf, j, a.tw);
+      }
+      // frequency of element m: j + m J, or for the 1024-point FFT
+      // slice + 8 (lane >> 2) + 64 m + 512 ((lane >> 1) & 1)
+      const int kb = PG::SWAP1K ? (warp >> 2) + 8 * (lane >> 2) + 512 * ((lane >> 1) & 1) : j;
+      constexpr int KS = PG::SWAP1K ? 64 : J;
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         if constexpr (!PG::SWAP)
           if ((m & 3) == 0) asm volatile("" ::: "memory");  // at most 4 loads in flight
-        const Q4<T> q = ldg_q4(a.mult + j + m * J);
+        const Q4<T> q = ldg_q4(a.mult + kb + m * KS);
         const T vr = v[m].re, vi = v[m].im;
         const T sh = -sg * q.z, sl = -sg * q.w;
         v[m] = {q.x * vr + ((q.y * vr - sl * vi) - sh * vi),
@@ -450,6 +601,10 @@ __global__ void __launch_bounds__(1024, 1)
                               tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
                               t3tab + 8 * slice);
       }
+      else if constexpr (PG::SWAP1K)
+        fft1024_swap<T, true, PG::XP, PG::XQ>(v, xw, lane, slice, quarter,
+                                              tlane + PG::T_TW + 16u * (uint32_t)slice,
+                                              tlane + PG::T_X2, t2tab);
       else
         fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
 
