@@ -280,12 +280,14 @@ def run_batch(args):
                                  stream=stream.cuda_stream)
     pts = sum(w.points for w in ws)
 
-    def run(n_steps):
+    def run(n_steps, tune=False):
         slots = []
         for s, w in zip(sims, ws):
             s.set_state(w.psi0)
             slots.append(D.dirac_batch_submit(batch, s.ctx, n_steps, w.dt))
         torch.cuda.synchronize()
+        if tune:  # CTA shapes of every class timed on its contexts (outside the timing)
+            D.dirac_batch_autotune(batch, 5)
         if world > 1:
             torch.distributed.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -300,7 +302,9 @@ def run_batch(args):
             D.dirac_batch_release(batch, sl)
         return max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
 
-    run(max(3, args.warmup))
+    run(max(3, args.warmup), tune=True)
+    shapes = {str(n): list(D.dirac_batch_launch_shape(batch, n, n)) for n in W.BATCH_SIZES
+              if any(w.nx == n for w in ws)}
     l0 = D.dirac_batch_launch_count(batch)
     with Clocks(local) as clk:
         ms = run(args.steps)
@@ -342,6 +346,7 @@ def run_batch(args):
         "config": {"workload": f"batch-mix-{count}", "precision": "c64 batched",
                    "sizes": {str(n): sum(1 for w in ws if w.nx == n) for n in W.BATCH_SIZES},
                    "points_per_step": pts, "steps_per_tick": args.tick,
+                   "autotuned_threads_xy": shapes,
                    "l2": "working set larger than L2 (no flush)"},
         "plain_c128_single_instance": {"value": plain, "unit": UNIT,
                                        "sample": f"one instance of each size, {plain_steps} steps, "

@@ -272,6 +272,22 @@ int dirac_batch_active(const dirac_batch *batch);
 /* Kernels the batch has enqueued (each kernel node of a replayed tick graph counts). */
 long dirac_batch_launch_count(const dirac_batch *batch);
 
+/* Batch autotuner: for every class (contexts of one grid size) with contexts still
+ * stepping, times each CTA shape of its x and y passes launched over all of those
+ * contexts at once (reps launches per shape, CUDA events on the batch's stream) and keeps
+ * the fastest for the class's later ticks. The timed launches read the states and write
+ * only the contexts' second state buffers, which hold nothing between steps, so no state
+ * changes. Call between ticks (it synchronises the batch's stream); DIRAC_EINVAL for
+ * reps < 1, DIRAC_ETIMEOUT if a bounded device wait ran out. */
+dirac_status dirac_batch_autotune(dirac_batch *batch, int reps);
+
+/* The CTA shapes, in dirac_set_launch terms (256, 512, 1024 threads), that the class of
+ * nx x ny contexts runs in this batch: the autotuner's choice, else the batch default
+ * (complex64 lines of 256 points or more: the persistent pass; otherwise 512).
+ * DIRAC_EINVAL if the batch has no such class. */
+dirac_status dirac_batch_launch_shape(const dirac_batch *batch, int nx, int ny, int *threads_x,
+                                      int *threads_y);
+
 const char *dirac_batch_last_error(const dirac_batch *batch);
 
 /* Waits for enqueued work and frees the batch (not the contexts). NULL is allowed. */

@@ -39,6 +39,7 @@ ABI_SYMBOLS = (
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
+    "dirac_batch_autotune", "dirac_batch_launch_shape",
 )
 
 
@@ -124,8 +125,11 @@ def lib():
         L.dirac_batch_poll.argtypes = [vp, i, C.POINTER(i)]
         L.dirac_batch_release.argtypes = [vp, i]
         L.dirac_batch_synchronize.argtypes = [vp]
+        L.dirac_batch_autotune.argtypes = [vp, i]
+        L.dirac_batch_launch_shape.argtypes = [vp, i, i, C.POINTER(i), C.POINTER(i)]
         for f in ("dirac_batch_create", "dirac_batch_submit", "dirac_batch_run",
-                  "dirac_batch_poll", "dirac_batch_release", "dirac_batch_synchronize"):
+                  "dirac_batch_poll", "dirac_batch_release", "dirac_batch_synchronize",
+                  "dirac_batch_autotune", "dirac_batch_launch_shape"):
             getattr(L, f).restype = C.c_int
         L.dirac_batch_active.argtypes = [vp]
         L.dirac_batch_active.restype = C.c_int
@@ -298,6 +302,20 @@ def dirac_batch_last_error(batch) -> str:
 def _bcheck(status, batch):
     if status != DIRAC_OK:
         raise DiracError(status, dirac_batch_last_error(batch))
+
+
+def dirac_batch_autotune(batch, reps: int = 10):
+    """Times every CTA shape of each class's passes over its stepping contexts and keeps
+    the fastest (no state changes)."""
+    _bcheck(lib().dirac_batch_autotune(batch, int(reps)), batch)
+
+
+def dirac_batch_launch_shape(batch, nx: int, ny: int):
+    """(threads_x, threads_y) in dirac_set_launch terms of the nx x ny class."""
+    tx, ty = C.c_int(0), C.c_int(0)
+    _bcheck(lib().dirac_batch_launch_shape(batch, int(nx), int(ny), C.byref(tx), C.byref(ty)),
+            batch)
+    return tx.value, ty.value
 
 
 def dirac_batch_create(budget_bytes: int, precision: int = DIRAC_C64, steps_per_tick: int = 32,

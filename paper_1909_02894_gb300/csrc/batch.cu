@@ -42,6 +42,7 @@ struct Class {
   cudaStream_t stream = nullptr;
   void* tw_x = nullptr;  // twiddle tables owned by the class (contexts come and go)
   void* tw_y = nullptr;
+  int opt[2] = {-1, -1};  // CTA shape of the x / y pass chosen by the autotuner (-1: default)
 };
 
 struct Slot {
@@ -184,9 +185,10 @@ static dirac_status launch_class_step(dirac_batch* b, Class& c, int k, cudaStrea
     a.inst = (const InstPtrs<T>*)c.d_tab + ((size_t)k * 2 + pass) * c.capacity;
     a.n_inst = c.d_count + k;
     a.inst_capacity = c.capacity;
-    // complex64 lines of 256 points or more: the persistent pass (its grid does not
-    // depend on the number of active instances); otherwise the 512-thread shape
-    const int opt = (sizeof(T) == 4 && a.L >= 256) ? 2 : 1;
+    // the autotuner's choice, else: complex64 lines of 256 points or more the persistent
+    // pass (its grid does not depend on the number of active instances), otherwise the
+    // larger shape
+    const int opt = c.opt[pass] >= 0 ? c.opt[pass] : (sizeof(T) == 4 && a.L >= 256) ? 2 : 1;
     BCK(launch_line_pass<T>(a, MODE_STEP, opt, st), "batched pass");
     b->launches += 1;
   }
@@ -293,6 +295,101 @@ static dirac_status run_tick(dirac_batch* b, int K) {
     }
   }
   return DIRAC_OK;
+}
+
+// Shapes worth timing for a pass over lines of L points (the launcher maps the others onto
+// these): complex64 256..4096 points also the persistent pass; lines of 128 points or
+// fewer and 4096-point lines have one non-persistent shape.
+template <typename T>
+static std::vector<int> shape_candidates(int L) {
+  std::vector<int> o;
+  if (L > 128 && L < 4096) o.push_back(0);
+  o.push_back(1);
+  if (sizeof(T) == 4 && L >= 256) o.push_back(2);
+  return o;
+}
+
+// Times every candidate shape of both passes of one class over its stepping contexts.
+// The launches read the states and write the contexts' second state buffers only (scratch
+// between steps): the x pass as in a step, the y pass reading the state as if transposed
+// (the same number of points), so no state changes.
+template <typename T>
+static dirac_status autotune_class(dirac_batch* b, Class& c, int reps, bool* changed) {
+  std::vector<int> m;
+  for (int s : c.members)
+    if (b->slots[s].state == 1 && b->slots[s].left > 0) m.push_back(s);
+  if (m.empty()) return DIRAC_OK;
+  const int n = (int)m.size();
+  std::vector<InstPtrs<T>> h(2 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    const dirac_ctx* x = b->slots[m[i]].ctx;
+    InstPtrs<T>& px = h[i];
+    InstPtrs<T>& py = h[(size_t)n + i];
+    px = InstPtrs<T>{};
+    py = InstPtrs<T>{};
+    px.in = py.in = (const Q4<T>*)x->psi;
+    px.out = py.out = (Q4<T>*)x->psiT;
+    px.beta = (const T*)x->beta1;
+    py.beta = (const T*)x->beta2T;
+    px.mult = (const Q4<T>*)x->mult_x;
+    py.mult = (const Q4<T>*)x->mult_y;
+    py.u_store = x->u_identity ? nullptr : (const Q4<T>*)x->u2_t;
+  }
+  InstPtrs<T>* d_tab = nullptr;
+  int* d_cnt = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  dirac_status st = DIRAC_OK;
+  auto cleanup = [&]() {
+    if (d_tab) cudaFree(d_tab);
+    if (d_cnt) cudaFree(d_cnt);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  cudaError_t e = cudaMalloc((void**)&d_tab, h.size() * sizeof(InstPtrs<T>));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&d_cnt, sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_tab, h.data(), h.size() * sizeof(InstPtrs<T>), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_cnt, &n, sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+    LinePassArgs<T> a{};
+    a.L = pass == 0 ? c.nx : c.ny;
+    a.n_lines = pass == 0 ? c.ny : c.nx;
+    a.sigma = pass;
+    a.tw = (const Cx<T>*)(pass == 0 ? c.tw_x : c.tw_y);
+    a.err = b->d_err;
+    a.inst = d_tab + (size_t)pass * n;
+    a.n_inst = d_cnt;
+    a.inst_capacity = n;
+    float best = 0.f;
+    int best_opt = -1;
+    for (int o : shape_candidates<T>(a.L)) {
+      e = launch_line_pass<T>(a, MODE_STEP, o, b->stream);  // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r)
+        e = launch_line_pass<T>(a, MODE_STEP, o, b->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) break;
+      b->launches += reps + 1;
+      if (best_opt < 0 || ms < best) {
+        best = ms;
+        best_opt = o;
+      }
+    }
+    if (e == cudaSuccess && best_opt != c.opt[pass]) {
+      c.opt[pass] = best_opt;
+      *changed = true;
+    }
+  }
+  if (e != cudaSuccess)
+    st = bfail(b, e == cudaErrorMemoryAllocation ? DIRAC_ENOMEM : DIRAC_ECUDA,
+               std::string("batch autotune: ") + cudaGetErrorString(e));
+  cleanup();
+  return st;
 }
 
 extern "C" {
@@ -460,6 +557,42 @@ int dirac_batch_active(const dirac_batch* b) {
 long dirac_batch_launch_count(const dirac_batch* b) { return b ? b->launches : 0; }
 
 const char* dirac_batch_last_error(const dirac_batch* b) { return b ? b->err.c_str() : ""; }
+
+dirac_status dirac_batch_autotune(dirac_batch* b, int reps) {
+  if (!b) return DIRAC_EINVAL;
+  if (reps < 1) return bfail(b, DIRAC_EINVAL, "reps must be >= 1");
+  BCK(cudaStreamSynchronize(b->stream), "batch autotune");
+  bool changed = false;
+  for (auto& kv : b->classes) {
+    dirac_status st = b->prec == DIRAC_C64 ? autotune_class<float>(b, kv.second, reps, &changed)
+                                           : autotune_class<double>(b, kv.second, reps, &changed);
+    if (st != DIRAC_OK) return st;
+  }
+  int flag = 0;
+  BCK(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+  if (flag) return bfail(b, DIRAC_ETIMEOUT, "a bounded device wait ran out in a timed pass");
+  if (changed && b->graph) {  // the next tick captures a graph with the new shapes
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_key.clear();
+  }
+  return DIRAC_OK;
+}
+
+dirac_status dirac_batch_launch_shape(const dirac_batch* b, int nx, int ny, int* threads_x,
+                                      int* threads_y) {
+  if (!b || !threads_x || !threads_y) return DIRAC_EINVAL;
+  auto it = b->classes.find(std::make_pair(nx, ny));
+  if (it == b->classes.end()) return DIRAC_EINVAL;
+  static const int th[3] = {256, 512, 1024};
+  const int L[2] = {nx, ny};
+  int* out[2] = {threads_x, threads_y};
+  for (int p = 0; p < 2; ++p) {
+    const int o = it->second.opt[p];
+    *out[p] = th[o >= 0 ? o : (b->prec == DIRAC_C64 && L[p] >= 256) ? 2 : 1];
+  }
+  return DIRAC_OK;
+}
 
 void dirac_batch_destroy(dirac_batch* b) {
   if (!b) return;

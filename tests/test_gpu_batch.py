@@ -64,6 +64,51 @@ def test_alone_equals_in_mix(prec):
             s.close()
 
 
+@pytest.mark.parametrize("prec", [D.DIRAC_C64, D.DIRAC_C128], ids=["c64", "c128"])
+def test_autotuned_batch_equals_alone_runs_with_its_shapes(prec):
+    """The batch autotuner times each class's CTA shapes on its contexts without changing
+    any state: after it, every context's result equals, bit for bit, the context stepped
+    alone with the shapes the autotuner chose for its class."""
+    sizes = [128, 256, 512, 1024, 256, 128]
+    steps = [20, 33, 17, 12, 40, 9]
+    ws = mix(11, sizes, steps)
+    batch = D.dirac_batch_create(64 << 30, prec, steps_per_tick=8)
+    sims, slots = [], []
+    try:
+        for w in ws:
+            s = D.Simulation(w, precision=prec)
+            s.set_state(w.psi0)
+            sims.append(s)
+            slots.append(D.dirac_batch_submit(batch, s.ctx, w.steps, w.dt))
+        with pytest.raises(D.DiracError) as e:
+            D.dirac_batch_autotune(batch, 0)
+        assert e.value.status == D.DIRAC_EINVAL
+        D.dirac_batch_autotune(batch, 3)
+        shapes = {n: D.dirac_batch_launch_shape(batch, n, n) for n in set(sizes)}
+        for n, (tx, ty) in shapes.items():
+            assert tx in (256, 512, 1024) and ty in (256, 512, 1024), (n, tx, ty)
+            if prec == D.DIRAC_C128:
+                assert tx != 1024 and ty != 1024
+        with pytest.raises(D.DiracError):
+            D.dirac_batch_launch_shape(batch, 64, 64)
+        while D.dirac_batch_active(batch):
+            D.dirac_batch_run(batch, 1)
+        D.dirac_batch_synchronize(batch)
+        for w, s, sl in zip(ws, sims, slots):
+            D.dirac_batch_release(batch, sl)
+            got = s.get_state()
+            with D.Simulation(w, precision=prec) as a:
+                D.dirac_set_launch(a.ctx, *shapes[w.nx])
+                a.set_state(w.psi0)
+                a.step(w.steps, w.dt)
+                ref = a.get_state()
+            assert np.array_equal(got, ref), (w.name, shapes[w.nx], W.rel_l2(got, ref))
+    finally:
+        D.dirac_batch_destroy(batch)
+        for s in sims:
+            s.close()
+
+
 def test_batch_matches_oracle_and_admits_late_arrivals():
     """A context submitted while others run is stepped from its own start and matches
     the oracle; the budget refuses an instance that does not fit."""
