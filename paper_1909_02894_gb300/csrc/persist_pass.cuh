@@ -57,11 +57,16 @@ struct PGeo {
   // work on points 512 k apart in the epilogue, reach different banks.
   static constexpr int PAD_EVERY = 512;
   static constexpr size_t STAGE_POINTS = SWAP ? L + L / PAD_EVERY : L + 1;
+  // Row pitch (points) of the staging buffer between lines: the transposed store gathers
+  // the same point of the LPI lines in consecutive lanes, so rows LPI apart in 16-byte
+  // slots of a 128-byte bank row must differ: pitch = 8 / LPI modulo 8 (any odd pitch for
+  // 16 lines).
+  static constexpr int SPITCH = SWAP ? L + 1 : L + (LPI <= 8 ? 8 / LPI : 1);
   static constexpr size_t F_RAW =
       SWAP ? ((size_t)2 * L * sizeof(Cx<T>) > STAGE_POINTS * sizeof(Q4<T>)
                   ? (size_t)2 * L * sizeof(Cx<T>) : STAGE_POINTS * sizeof(Q4<T>))
-      : SWAP1K ? (XBUF_BYTES > (size_t)LPI * STAGE_POINTS * sizeof(Q4<T>)
-                      ? XBUF_BYTES : (size_t)LPI * STAGE_POINTS * sizeof(Q4<T>))
+      : SWAP1K ? (XBUF_BYTES > (size_t)LPI * SPITCH * sizeof(Q4<T>)
+                      ? XBUF_BYTES : (size_t)LPI * SPITCH * sizeof(Q4<T>))
            : G::SMEM;
   static constexpr size_t F_BYTES = ((F_RAW + 127) / 128) * 128;
   static constexpr size_t PSI_BYTES = (size_t)LPI * L * sizeof(Q4<T>);
@@ -88,6 +93,7 @@ struct PGeo {
   static_assert(sizeof(T) == 4, "persistent pass is complex64 only");
   static_assert(G::THREADS == THREADS, "group must fill the CTA");
   static_assert(SMEM <= 227 * 1024, "shared memory budget");
+  static_assert(SWAP || F_BYTES >= (size_t)LPI * SPITCH * sizeof(Q4<T>), "staging buffer");
   static_assert(SMEM > 227 * 1024 / 2, "one CTA per SM (the tensor-memory allocation relies on it)");
   static_assert(THREADS / 32 / 4 * 2 * E == 128, "tensor-memory layout");
   static_assert(BETA_PITCH % 16 == 0 && U_PITCH % 16 == 0 && OFF_BAR % 16 == 0, "bulk copy");
@@ -641,7 +647,7 @@ __global__ void __launch_bounds__(1024, 1)
             stage[PG::spos(i)] = o;
           }
         } else {
-          Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * (L + 1)) + c;
+          Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * PG::SPITCH) + c;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             float pk[E];
@@ -688,7 +694,7 @@ __global__ void __launch_bounds__(1024, 1)
       for (int q = 0; q < NIT; ++q) {
         const int idx = tid + q * PG::THREADS;
         const int l = idx / L, i = idx - l * L;
-        a.out[gfirst + idx] = stage[(size_t)l * (L + 1) + PG::spos(i)];
+        a.out[gfirst + idx] = stage[(size_t)l * PG::SPITCH + PG::spos(i)];
       }
     } else if (!failed) {
       const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(psmem);
@@ -703,7 +709,7 @@ __global__ void __launch_bounds__(1024, 1)
         for (int q = 0; q < NIT; ++q) {
           const int itm = tid + q * PG::THREADS;
           const int gg = itm % GL, owner = gg / LPI;
-          const uint32_t off = (uint32_t)(((gg - owner * LPI) * (L + 1) + PG::spos(i0 + itm / GL)) *
+          const uint32_t off = (uint32_t)(((gg - owner * LPI) * PG::SPITCH + PG::spos(i0 + itm / GL)) *
                                           sizeof(Q4<T>));
           val[q] = ld_dsmem_q4<T>(mapa_shared(local, owner) + off);
         }
@@ -711,7 +717,7 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
         for (int q = 0; q < NIT; ++q) {
           const int itm = tid + q * PG::THREADS;
-          val[q] = stage[(size_t)(itm % GL) * (L + 1) + PG::spos(i0 + itm / GL)];
+          val[q] = stage[(size_t)(itm % GL) * PG::SPITCH + PG::spos(i0 + itm / GL)];
         }
       }
 #pragma unroll
