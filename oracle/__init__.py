@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the benchma
 CPU-baseline leg import this package. The product path (the CUDA library and its
 binding) never does. The oracle shares no code with the CUDA path.
 
-``build()`` compiles ``dirac_oracle.c`` with gcc (``-O2 -ffp-contract=off -fopenmp``).
+``build()`` compiles ``dirac_oracle.c`` with gcc (``-O3 -ffp-contract=off -fopenmp``).
 """
 from __future__ import annotations
 
@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB_PATH) >= os.path.getmtime(os.path.join(HERE, "dirac_oracle.h"))):
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
            "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True, cwd=HERE)
     os.replace(tmp, LIB_PATH)
@@ -76,10 +76,12 @@ def lib():
                                                  C.c_double, C.c_long, C.c_int, C.c_int, dp,
                                                  dp, dp, C.c_int, dp, dp, dp]
         L.oracle_threads.argtypes = []
+        L.oracle_set_threads.argtypes = [C.c_int]
         for f in ("oracle_fft", "oracle_deriv", "oracle_coefficients", "oracle_half_step",
                   "oracle_run", "oracle_observables", "oracle_modes_evolve", "oracle_threads",
                   "oracle_run_scheme", "oracle_modes_evolve_scheme", "oracle_apply_A",
-                  "oracle_bessel_j", "oracle_run_poly", "oracle_run_cn"):
+                  "oracle_bessel_j", "oracle_run_poly", "oracle_run_cn",
+                  "oracle_set_threads"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -269,3 +271,8 @@ def modes_evolve(prob: Problem, g00, g11, g22, dt, n_steps, modes, ix, iy, schem
 
 def threads() -> int:
     return lib().oracle_threads()
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads for later oracle calls (for single-thread timing)."""
+    _check(lib().oracle_set_threads(int(n)), "set_threads")

@@ -16,8 +16,10 @@
  * exp(-i dt xi Lambda) of eq. second_scheme in the alpha^i eigenbasis equals
  * exp(-i dt xi sigma_j) in the original basis because Pi Lambda Pi^dagger = sigma_j.
  *
- * Parity status: pinned (see the oracle tests) except the covariant spin connection
- * and the absorbing-layer profile values, which only invariants check.
+ * Parity status: every function is pinned by the oracle tests. The absorbing-layer
+ * profile is checked point by point against the Sec. 3 closed forms (all six types,
+ * theta = 0 and theta != 0); the covariant spin connection by the Hermiticity of w H
+ * (a real weighted energy) and by a dense Hamiltonian on a tiny curved grid.
  */
 #include "dirac_oracle.h"
 
@@ -40,6 +42,14 @@ int oracle_threads(void) {
 #else
   return 1;
 #endif
+}
+
+int oracle_set_threads(int n) {
+  if (n < 1) return -1;
+#ifdef _OPENMP
+  omp_set_num_threads(n);
+#endif
+  return 0;
 }
 
 /* ---------------------------------------------------------------------------------

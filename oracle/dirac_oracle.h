@@ -12,10 +12,10 @@
  * [2][ny][nx] double complex (interleaved re, im), component-major.
  * Every function returns 0 on success and a negative value on invalid arguments.
  *
- * Parity status: every function below is pinned by the oracle tests except two
- * modelling choices, which are checked only by invariants: the covariant spin
- * connection (conserved weighted norm) and the absorbing-layer profile values
- * (monotone decay, and no effect where the layer is empty).
+ * Parity status: every function below is pinned by the oracle tests, including the
+ * absorbing-layer profile (point by point against the Sec. 3 closed forms) and the
+ * covariant spin connection (w H Hermitian: the weighted energy is real; a dense
+ * curved-space Hamiltonian on a tiny grid).
  */
 #ifndef DIRAC_ORACLE_H
 #define DIRAC_ORACLE_H
@@ -127,6 +127,9 @@ int oracle_modes_evolve_scheme(const oracle_params *p, double g00, double g11, d
 
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 int oracle_threads(void);
+
+/* Sets the number of OpenMP threads for later calls (n >= 1; ignored without OpenMP). */
+int oracle_set_threads(int n);
 
 #ifdef __cplusplus
 }

@@ -877,3 +877,167 @@ def test_energy_with_potentials_flat_parseval(oracle_lib):
     ref = (np.vdot(h0, Hh0) + np.vdot(h1, Hh1)) * h * h / n ** 2
     assert abs(obs["energy"] - ref.real) <= 1e-12 * abs(ref)
     assert abs(obs["energy_imag"]) <= 1e-12 * abs(ref)
+
+
+# ------------------------------------------- absorbing-layer profiles, closed form
+def _sigma_profile(ptype, s, delta, s0):
+    """Sec. 3 table of absorbing functions Sigma evaluated at s = |x| - L in [-delta, 0):
+    I s0 (s+delta)^2, II s0 (s+delta)^3, III -s0/s, IV s0/s^2, V -s0/s - s0/delta,
+    VI s0/s^2 - s0/delta^2."""
+    return {1: lambda: s0 * (s + delta) ** 2,
+            2: lambda: s0 * (s + delta) ** 3,
+            3: lambda: -s0 / s,
+            4: lambda: s0 / s ** 2,
+            5: lambda: -s0 / s - s0 / delta,
+            6: lambda: s0 / s ** 2 - s0 / delta ** 2}[ptype]()
+
+
+def _closed_form_inv_S(n, a, width, ptype, s0, theta):
+    """1/S(x_i) at every grid point x_i = -a + i h from the physical coordinate: the layer
+    is L* <= |x| <= L with L = a, L* = a - width h (Sec. 3); S = 1 + e^{i theta} Sigma(|x|-L).
+    The point x_0 = -a lies at |x| = L, where the singular types (III-VI) give S = inf,
+    i.e. 1/S = 0, and types I/II their finite limit."""
+    x = W.grid_1d(n, a)
+    h = 2.0 * a / n
+    L, Ls = a, a - width * h
+    delta = L - Ls
+    out = np.ones(n, dtype=complex)
+    for i, xi in enumerate(x):
+        ax_ = abs(xi)
+        if width == 0 or ax_ < Ls - 1e-9 * h:
+            continue
+        s = ax_ - L
+        if abs(s) <= 1e-9 * h:
+            if ptype >= 3:
+                out[i] = 0.0
+                continue
+            s = 0.0
+        out[i] = 1.0 / (1.0 + np.exp(1j * theta) * _sigma_profile(ptype, s, delta, s0))
+    return out
+
+
+@pytest.mark.parametrize("ptype", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("theta", [0.0, 0.4])
+def test_pml_profile_matches_the_closed_form_at_every_point(oracle_lib, ptype, theta):
+    """b^j = a^j / S^j (Sec. 5.2) at every grid point of both axes, both sides, against
+    the Sec. 3 profile evaluated at the physical coordinate; a^j from its closed form."""
+    nx, ny, ax, ay = 32, 16, 4.0, 3.0
+    wx, wy, s0, c = 5, 3, 0.7, 1.3
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g00 = 1.0 + 0.2 * np.exp(-(X ** 2 + Y ** 2))
+    g11 = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + Y ** 2))
+    g22 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y - 0.3) ** 2))
+    prob = problem(oracle_lib, nx, ny, ax, ay, c=c, g00=g00, g11=g11, g22=g22,
+                   pml_wx=wx, pml_wy=wy, pml_type=ptype, sigma0=s0, theta=theta)
+    co = oracle_lib.coefficients(prob)
+    a1 = c * np.sqrt(g00 / g11)
+    a2 = c * np.sqrt(g00 / g22)
+    ref1 = a1 * _closed_form_inv_S(nx, ax, wx, ptype, s0, theta)[None, :]
+    ref2 = a2 * _closed_form_inv_S(ny, ay, wy, ptype, s0, theta)[:, None]
+    assert np.abs(co["b1"] - ref1).max() <= 1e-13 * np.abs(a1).max()
+    assert np.abs(co["b2"] - ref2).max() <= 1e-13 * np.abs(a2).max()
+    # the layer holds exactly the outer `width` points on each side plus the inner edge
+    # |x| = L* itself, where only types I, II, V and VI vanish
+    layer_x = np.nonzero(np.abs(ref1[0] - a1[0]) > 1e-15)[0]
+    edge_free = ptype in (1, 2, 5, 6)
+    expect = set(range(0, wx + (0 if edge_free else 1))) | \
+        set(range(nx - wx + (1 if edge_free else 0), nx))
+    assert set(layer_x) == expect
+    if theta != 0.0:
+        assert np.abs(co["b1"].imag).max() > 1e-3
+
+
+# ------------------------------------------------ energy with the spin connection
+def _dense_hamiltonian(nx, ny, ax, ay, g00, g11, g22, mass, c, V=None, Ax=None, Ay=None,
+                       omega_scale=1.0):
+    """H of Sec. 2.2 (eq. dirac_simplified with eq. alpha_form) as a dense 2N x 2N matrix:
+    -i sum_j a^j sigma_j (D_j + Omega_j) + meff sigma_z + V - sum_j a^j A_j sigma_j, with
+    D_j the spectral derivative from explicit DFT matrices and Omega_j = 1/2 d_j ln(w a^j)
+    from numpy's FFT (omega_scale multiplies it, for the negative controls)."""
+    npt = nx * ny
+    a1 = c * np.sqrt(g00 / g11)
+    a2 = c * np.sqrt(g00 / g22)
+    me = mass * c * c * np.sqrt(g00)
+    w = np.sqrt(g11 * g22 / g00)
+    omx = omega_scale * 0.5 * np.real(np_deriv(np.log(w * a1), 0, ax))
+    omy = omega_scale * 0.5 * np.real(np_deriv(np.log(w * a2), 1, ay))
+
+    def dmat(n, a):
+        kk = np.arange(n)
+        Fm = np.exp(-2j * np.pi * np.outer(kk, kk) / n)
+        return np.conj(Fm) / n @ np.diag(1j * xi_vec(n, a)) @ Fm
+
+    Dx = np.kron(np.eye(ny), dmat(nx, ax))
+    Dy = np.kron(dmat(ny, ay), np.eye(nx))
+    d = lambda f: np.diag(np.asarray(f, dtype=complex).ravel())
+    Z = np.zeros((npt, npt), dtype=complex)
+    Vm = d(V) if V is not None else Z
+    Axm = d(a1 * Ax) if Ax is not None else Z
+    Aym = d(a2 * Ay) if Ay is not None else Z
+    # sigma_x (u, v) = (v, u); sigma_y (u, v) = (-i v, i u)
+    Phx = Dx + d(omx)
+    Phy = Dy + d(omy)
+    H = np.zeros((2 * npt, 2 * npt), dtype=complex)
+    H[:npt, :npt] = d(me) + Vm
+    H[npt:, npt:] = -d(me) + Vm
+    H[:npt, npt:] = -1j * d(a1) @ Phx + -1j * d(a2) @ (-1j * Phy) - Axm - (-1j) * Aym
+    H[npt:, :npt] = -1j * d(a1) @ Phx + -1j * d(a2) @ (1j * Phy) - Axm - 1j * Aym
+    return H, np.tile(w.ravel(), 2)
+
+
+def test_energy_matches_a_dense_curved_hamiltonian(oracle_lib):
+    """energy + i energy_imag = h_x h_y psi^dagger diag(w) H psi with the dense H above,
+    on a curved 8 x 4 grid with a non-zero covariant connection, mass and potentials."""
+    nx, ny, ax, ay = 8, 4, 3.0, 2.0
+    X, Y = W.mesh(nx, ny, ax, ay)
+    g00 = 1.0 + 0.2 * np.exp(-(X ** 2 + Y ** 2))
+    g11 = 1.0 + 0.3 * np.exp(-((X - 0.5) ** 2 + Y ** 2))
+    g22 = 1.0 + 0.1 * np.exp(-(X ** 2 + (Y - 0.3) ** 2))
+    mass, c = 0.7, 1.1
+    rng = np.random.default_rng(77)
+    V, Ax, Ay = (rng.uniform(-0.5, 0.5, (ny, nx)) for _ in range(3))
+    psi = W.random_state(nx, ny, 12)
+    prob = problem(oracle_lib, nx, ny, ax, ay, mass=mass, c=c, g00=g00, g11=g11, g22=g22)
+    prob.V, prob.Ax, prob.Ay = V, Ax, Ay
+    co = oracle_lib.coefficients(prob)
+    assert np.abs(co["omx"]).max() > 1e-2 and np.abs(co["omy"]).max() > 1e-2
+    got = oracle_lib.observables(prob, psi)
+    H, w = _dense_hamiltonian(nx, ny, ax, ay, g00, g11, g22, mass, c, V, Ax, Ay)
+    v = psi.ravel()
+    e = (2 * ax / nx) * (2 * ay / ny) * np.vdot(v, w * (H @ v))
+    assert abs(got["energy"] - e.real) <= 1e-12 * abs(e)
+    assert abs(got["energy_imag"] - e.imag) <= 1e-12 * abs(e)
+    # the test's own model is sensitive to the connection: dropping it or flipping its
+    # sign moves the energy by far more than the tolerance
+    for scale in (0.0, -1.0):
+        Hb, _ = _dense_hamiltonian(nx, ny, ax, ay, g00, g11, g22, mass, c, V, Ax, Ay, scale)
+        eb = (2 * ax / nx) * (2 * ay / ny) * np.vdot(v, w * (Hb @ v))
+        assert abs(eb - e) > 1e-3 * abs(e)
+
+
+@pytest.mark.parametrize("mass,pot", [(0.0, False), (0.8, True)])
+def test_energy_is_real_for_the_covariant_connection(oracle_lib, mass, pot):
+    """With w = sqrt(g11 g22 / g00), the operator w H is Hermitian exactly when
+    Omega_j = 1/2 d_j ln(w a^j) (the anti-Hermitian part of -i w a^j sigma_j d_j is
+    (i/2) d_j(w a^j) sigma_j, which the connection term -i w a^j Omega_j sigma_j must
+    cancel; mass and potentials are Hermitian). So the weighted energy of any smooth state
+    is real to spectral accuracy with the covariant connection, and far from real without
+    it -- a pin of the connection's sign and factor that uses no formula of the oracle."""
+    n, a = 64, 8.0
+    X, Y = W.mesh(n, n, a, a)
+    g00 = 1.0 + 0.15 * W.gaussian(X, Y, 0.5, -0.3, 1.8)
+    g11 = 1.0 + 0.3 * W.gaussian(X, Y, -0.8, 0.4, 1.5)
+    g22 = 1.2 + 0.2 * W.gaussian(X, Y, 0.6, 0.9, 1.6)
+    psi = W.wave_packet(n, n, a, a, 1.3, (1.0, -0.5), x0=(0.4, -0.2))
+    psi[1] = 0.5 * W.wave_packet(n, n, a, a, 1.1, (-0.7, 0.3), x0=(-0.5, 0.6))[0]
+    kw = dict(mass=mass, c=1.0, g00=g00, g11=g11, g22=g22)
+    prob = problem(oracle_lib, n, n, a, a, **kw)
+    if pot:
+        prob.V = 0.3 * W.gaussian(X, Y, 0.0, 0.0, 2.0)
+        prob.Ax = 0.2 * W.gaussian(X, Y, 1.0, 0.0, 2.0)
+        prob.Ay = -0.1 * W.gaussian(X, Y, 0.0, 1.0, 2.0)
+    cov = oracle_lib.observables(prob, psi)
+    assert abs(cov["energy_imag"]) <= 1e-11 * abs(cov["energy"]), cov
+    none = oracle_lib.observables(problem(oracle_lib, n, n, a, a, conn=oracle_lib.CONN_NONE,
+                                          **kw), psi)
+    assert abs(none["energy_imag"]) >= 1e-4 * abs(none["energy"]), none
