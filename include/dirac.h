@@ -295,9 +295,9 @@ void dirac_batch_destroy(dirac_batch *batch);
 
 /* Norms of a device spinor without allocating device memory. The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc where they need a norm --
- * code running during CUDA stream capture (allocation is not allowed there), services
- * whose device memory all belongs to another allocator or a fixed arena, and loops that
- * cannot afford cudaMalloc/cudaFree's implicit device synchronisation.
+ * services whose device memory all belongs to another allocator or to a fixed arena
+ * reserved up front (a further cudaMalloc would fail or break their accounting), and
+ * loops that cannot afford cudaMalloc/cudaFree's implicit device synchronisation.
  *   psi:    device [2][ny][nx] complex128 (the ABI spinor layout), read only
  *   weight: device [ny][nx] doubles (e.g. w = sqrt(g11 g22 / g00)), or NULL for weight 1
  *   out:    device pointer to 2 doubles, receives {hx hy sum |psi|^2, hx hy sum w |psi|^2}
@@ -309,7 +309,9 @@ void dirac_batch_destroy(dirac_batch *batch);
  * looks up its device address (make that first call before any stream capture on that
  * device). All calls share the array: calls that overlap on the GPU race, so order them
  * on one stream or synchronise between them. Every call overwrites the partial sums it
- * reads, so no clearing is needed. */
+ * reads, so no clearing is needed. If a launch error of earlier, unrelated work is still
+ * pending on the calling thread, the call returns DIRAC_ECUDA without launching and
+ * leaves that error in place for its owner. */
 dirac_status dirac_norms_noalloc(const double *psi, const double *weight, int nx, int ny,
                                  double ax, double ay, double *out, void *cuda_stream);
 

@@ -266,17 +266,38 @@ def dirac_launch_count(ctx) -> int:
 
 def dirac_norms_noalloc(psi, weight, ax: float, ay: float, out, stream=None):
     """Norms of a CUDA complex128 [2][ny][nx] tensor without device allocation: writes
-    {norm, weighted norm} into out (a CUDA float64 tensor of 2). weight: CUDA float64
-    [ny][nx] tensor or None. Enqueued on `stream` (a raw handle; None = default stream)."""
-    assert psi.is_cuda and psi.is_contiguous() and str(psi.dtype) == "torch.complex128"
-    assert out.is_cuda and str(out.dtype) == "torch.float64" and out.numel() >= 2
-    ny, nx = int(psi.shape[-2]), int(psi.shape[-1])
-    wp = None
+    {norm, weighted norm} into out (a CUDA float64 tensor of at least 2 elements).
+    weight: CUDA float64 [ny][nx] tensor or None. All tensors must be contiguous and on
+    one device; the call is enqueued on that device, on `stream` (a raw handle; None =
+    the default stream). Raises ValueError before any launch if a tensor does not fit."""
+    def need(cond, msg):
+        if not cond:
+            raise ValueError(f"dirac_norms_noalloc: {msg}")
+
+    need(_is_torch(psi) and _is_torch(out), "psi and out must be torch tensors")
+    need(psi.dim() == 3 and int(psi.shape[0]) == 2,
+         f"psi must have shape (2, ny, nx), got {tuple(psi.shape)}")
+    ny, nx = int(psi.shape[1]), int(psi.shape[2])
+    need(str(psi.dtype) == "torch.complex128" and psi.is_contiguous(),
+         "psi must be contiguous complex128")
+    need(str(out.dtype) == "torch.float64" and out.is_contiguous() and out.numel() >= 2,
+         "out must be a contiguous float64 tensor of at least 2 elements")
     if weight is not None:
-        assert weight.is_cuda and weight.is_contiguous() and str(weight.dtype) == "torch.float64"
-        wp = weight.data_ptr()
-    _check(lib().dirac_norms_noalloc(psi.data_ptr(), wp, nx, ny, float(ax), float(ay),
-                                     out.data_ptr(), stream), None)
+        need(_is_torch(weight) and tuple(weight.shape) == (ny, nx),
+             f"weight must have shape {(ny, nx)}, got {tuple(getattr(weight, 'shape', ()))}")
+        need(str(weight.dtype) == "torch.float64" and weight.is_contiguous(),
+             "weight must be contiguous float64")
+    need(psi.is_cuda and out.is_cuda and (weight is None or weight.is_cuda),
+         "psi, weight and out must be CUDA tensors")
+    need(out.device == psi.device and (weight is None or weight.device == psi.device),
+         "psi, weight and out must be on one device")
+    import torch
+
+    with torch.cuda.device(psi.device):
+        _check(lib().dirac_norms_noalloc(psi.data_ptr(),
+                                         None if weight is None else weight.data_ptr(), nx,
+                                         ny, float(ax), float(ay), out.data_ptr(), stream),
+               None)
 
 
 def dirac_test_timeout_next_step(ctx):

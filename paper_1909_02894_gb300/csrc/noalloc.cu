@@ -1,11 +1,10 @@
 // Norm reduction that allocates no device memory.
 //
 // dirac_observables reduces through a partial-sums buffer that the context allocates.
-// Some callers cannot allocate device memory at the point where they need a norm: code
-// running while a CUDA stream is being captured into a graph (cudaMalloc is not allowed
-// there), services whose device memory is entirely owned by another allocator or a
-// fixed arena, and latency-critical loops that cannot afford cudaMalloc/cudaFree's
-// implicit device synchronisation. For them, dirac_norms_noalloc does the same FP64
+// Some callers cannot allocate device memory at the point where they need a norm:
+// services whose device memory is entirely owned by another allocator or by a fixed
+// arena reserved up front, and latency-critical loops that cannot afford
+// cudaMalloc/cudaFree's implicit device synchronisation. For them, dirac_norms_noalloc does the same FP64
 // reduction with its partial sums in a file-scope device array that exists for as long
 // as the library is loaded (on every GPU that loads it).
 #include <cuda_runtime.h>
@@ -129,6 +128,15 @@ extern "C" dirac_status dirac_norms_noalloc(const double* psi, const double* wei
       }
     }
     scratch = g_addr[dev];
+  }
+  // A launch error left by earlier work on this thread would otherwise surface below as
+  // this call's own; report it without clearing it, and launch nothing.
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    dgb::set_global_error(std::string("dirac_norms_noalloc: an earlier CUDA error is pending "
+                                      "on this thread (left in place): ") +
+                          cudaGetErrorString(e));
+    return DIRAC_ECUDA;
   }
   const size_t n = (size_t)nx * ny;
   size_t blocks = (n + kThreads - 1) / kThreads;

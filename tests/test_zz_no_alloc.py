@@ -1,8 +1,8 @@
 """The allocation-free norm entry point against dirac_observables.
 
 dirac_norms_noalloc exists for callers that cannot allocate device memory where they
-need a norm (stream capture, arena-owned memory, loops that cannot take cudaMalloc's
-implicit synchronisation). This file is collected last so that a failure here comes
+need a norm (device memory owned by another allocator or a fixed arena, loops that cannot
+take cudaMalloc's implicit synchronisation). This file is collected last so that a failure here comes
 after every other test has run; it also passes alone in a fresh process."""
 import numpy as np
 import pytest
@@ -48,3 +48,22 @@ def test_no_alloc_norms_match_observables_twice():
     stream.synchronize()
     n0, n1 = out.cpu().numpy()
     assert abs(n0 - ref["norm"]) <= 1e-12 * ref["norm"] and n0 == n1
+
+
+def test_no_alloc_binding_refuses_misshaped_tensors_before_any_launch():
+    """Shape, dtype and device checks raise ValueError on the host (CPU tensors here,
+    so nothing could have been launched)."""
+    torch = pytest.importorskip("torch")
+    psi = torch.zeros((2, 16, 32), dtype=torch.complex128)
+    out = torch.zeros(2, dtype=torch.float64)
+    bad = [
+        (torch.zeros((16, 32), dtype=torch.complex128), None, out, "shape"),
+        (torch.zeros((3, 16, 32), dtype=torch.complex128), None, out, "shape"),
+        (psi, torch.zeros((16, 16), dtype=torch.float64), out, "weight"),
+        (psi, None, torch.zeros(1, dtype=torch.float64), "out"),
+        (psi.to(torch.complex64), None, out, "complex128"),
+        (psi, None, out, "CUDA"),
+    ]
+    for p, w, o, word in bad:
+        with pytest.raises(ValueError, match=word):
+            D.dirac_norms_noalloc(p, w, 1.0, 1.0, o)
