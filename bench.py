@@ -12,6 +12,13 @@ larger than L2, so no flush is needed between timed steps.
 Prints one JSON line. The path does not shard: with N > 1 each rank runs an
 independent replica and `value` sums the ranks ("replicas only", weak scaling).
 The reference arm times the FP64 CPU oracle on the host cores on a bounded sample.
+
+At N = 1 the default line also carries, each with its error against the FP64 oracle:
+`rel_l2_vs_oracle` of the 4096^2 grid itself (whole grid, a few steps); `batch`, the
+256-instance uneven mix (128^2..1024^2) stepped 2000 times in complex64 beside the plain
+complex128 single-instance path (their ratio, per-size rel-L2 of batched and plain
+results); and `serving`, a short window of the 200 req/s strained-graphene stream through
+the continuous-batching loop (p50/p99 latency, throughput, clocks, FP64 check).
 """
 from __future__ import annotations
 
@@ -233,182 +240,327 @@ def run_reference(args, wl_name):
     return 0
 
 
-def cpu_baseline(w, scheme="printed", degree=8):
-    """Oracle timing on a bounded sample of the same workload (about 10-30 s of CPU)."""
+def cpu_baseline(w, scheme="printed", degree=8, check_steps=0):
+    """Oracle timing on a bounded sample of the same workload (about 10-30 s of CPU): the
+    difference of a k-step and a 1-step run on all host cores, k = max(2,
+    check_steps), and the same on one core (on the 1024^2 grid of the recipe when the
+    workload is larger). Also returns the oracle's state after max(2, check_steps) steps
+    from psi0 (for the rel-L2 of the GPU result)."""
     import oracle
 
     oracle.build()
-    prob = oracle.Problem.from_workload(w)
 
-    def run(n):
-        if scheme == "cn":
-            return oracle.run_cn(prob, w.psi0, w.dt, n, tol=1e-14)[0]
-        if scheme in ("taylor", "chebyshev"):
-            fam = oracle.POLY_TAYLOR if scheme == "taylor" else oracle.POLY_CHEBYSHEV
-            return oracle.run_poly(prob, w.psi0, w.dt, n, fam, degree)
-        return oracle.run(prob, w.psi0, w.dt, n, scheme=1 if scheme == "symmetric" else 0)
+    def runner(wl):
+        prob = oracle.Problem.from_workload(wl)
 
+        def run(n):
+            if scheme == "cn":
+                return oracle.run_cn(prob, wl.psi0, wl.dt, n, tol=1e-14)[0]
+            if scheme in ("taylor", "chebyshev"):
+                fam = oracle.POLY_TAYLOR if scheme == "taylor" else oracle.POLY_CHEBYSHEV
+                return oracle.run_poly(prob, wl.psi0, wl.dt, n, fam, degree)
+            return oracle.run(prob, wl.psi0, wl.dt, n, scheme=1 if scheme == "symmetric" else 0)
+        return run
+
+    k = max(2, check_steps)
+    run = runner(w)
     t0 = time.perf_counter()
     run(1)
     t1 = time.perf_counter()
-    run(2)
+    state = run(k)
     t2 = time.perf_counter()
-    per_step = max((t2 - t1) - (t1 - t0), 1e-9)
-    return {"value": w.nx * w.ny / per_step, "unit": UNIT, "cores": oracle.threads(),
-            "kind": "oracle",
-            "sample": f"difference of 2-step and 1-step FP64 oracle runs on {w.name}"}
+    per_step = max(((t2 - t1) - (t1 - t0)) / (k - 1), 1e-9)
+    cores = oracle.threads()
+    rec = {"value": w.nx * w.ny / per_step, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"difference of {k}-step and 1-step FP64 oracle runs on {w.name}, "
+                     f"divided by {k - 1}"}
+    # one core, on a smaller grid of the same recipe when the full grid is large
+    small = w
+    if w.nx * w.ny > 1024 * 1024 and w.name.startswith("large-"):
+        small = W.large_4096(n=1024, steps=1)
+    try:
+        oracle.set_threads(1)
+        run1 = runner(small)
+        t0 = time.perf_counter()
+        run1(1)
+        t1 = time.perf_counter()
+        run1(2)
+        t2 = time.perf_counter()
+        rec["single_thread"] = {
+            "value": small.nx * small.ny / max((t2 - t1) - (t1 - t0), 1e-9), "unit": UNIT,
+            "cores": 1, "sample": f"difference of 2-step and 1-step runs on {small.name}"}
+    finally:
+        oracle.set_threads(cores)
+    return rec, state
 
 
-def run_batch(args):
-    """Batched uneven mix: 256 instances (128^2..1024^2, weights 0.4/0.3/0.2/0.1), each
-    stepped `--steps` times (default 2000) in one batch of graph-captured ticks, complex64;
-    beside it the plain complex128 single-instance path, each instance alone."""
+def plain_c128_rate(w, stream, steps=50):
+    """Point-steps/s of the plain complex128 single-instance path on one workload (3
+    untimed steps, then `steps` steps timed with CUDA events on the context's stream)."""
     import torch
 
     import paper_1909_02894_gb300 as D
 
-    world, rank, local = dist_setup(args)
-    torch.cuda.set_device(local)
-    if world > 1:  # independent replicas of the whole mix, one per rank
-        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    with D.Simulation(w, precision=D.DIRAC_C128, stream=stream.cuda_stream) as s:
+        s.set_state(w.psi0)
+        s.step(3, w.dt)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps, w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return w.points * steps / (e0.elapsed_time(e1) * 1e-3)
+
+
+# Steps of the per-size oracle check of batched results: as many as keep the oracle's
+# share of the bench to about 15 s on the host cores.
+BATCH_CHECK_STEPS = {128: 1000, 256: 500, 512: 200, 1024: 100}
+
+
+def batch_record(args, stream, steps, world=1, check=True):
+    """Batched uneven mix (256 instances, 128^2..1024^2 with weights 0.4/0.3/0.2/0.1),
+    each stepped `steps` times in one batch of graph-captured ticks, complex64; beside it
+    the plain complex128 single-instance path on one instance of each size (each alone),
+    and, per size, the rel-L2 of a batched result and of the plain complex128 result
+    against the FP64 oracle."""
+    import torch
+
+    import paper_1909_02894_gb300 as D
+
     count = args.batch_count
-    ws = W.batch_mix(count=count, steps=args.steps)
-    stream = torch.cuda.Stream()
+    ws = W.batch_mix(count=count, steps=steps)
     sims = [D.Simulation(w, precision=D.DIRAC_C64, stream=stream.cuda_stream) for w in ws]
     budget = sum(D.dirac_footprint_bytes(w.nx, w.ny) for w in ws) + (1 << 20)
     batch = D.dirac_batch_create(budget, D.DIRAC_C64, steps_per_tick=args.tick,
                                  stream=stream.cuda_stream)
     pts = sum(w.points for w in ws)
-
-    def run(n_steps, tune=False):
-        slots = []
-        for s, w in zip(sims, ws):
-            s.set_state(w.psi0)
-            slots.append(D.dirac_batch_submit(batch, s.ctx, n_steps, w.dt))
-        torch.cuda.synchronize()
-        if tune:  # CTA shapes of every class timed on its contexts (outside the timing)
-            D.dirac_batch_autotune(batch, 5)
-        if world > 1:
-            torch.distributed.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        while D.dirac_batch_active(batch):
-            D.dirac_batch_run(batch, 1)
-        e1.record(stream)
-        D.dirac_batch_synchronize(batch)
-        torch.cuda.synchronize()
-        for sl in slots:
-            D.dirac_batch_release(batch, sl)
-        return max_over_ranks(e0.elapsed_time(e1), world, device="cuda")
-
-    run(max(3, args.warmup), tune=True)
-    shapes = {str(n): list(D.dirac_batch_launch_shape(batch, n, n)) for n in W.BATCH_SIZES
-              if any(w.nx == n for w in ws)}
-    l0 = D.dirac_batch_launch_count(batch)
-    with Clocks(local) as clk:
-        ms = run(args.steps)
-    value = whole_job_value(pts, args.steps, world, ms)
-    # plain complex128 path, each instance alone, on a bounded sample (one of each size)
-    sample, seen = [], set()
-    for w in ws:
-        if w.nx not in seen:
-            seen.add(w.nx)
-            sample.append(w)
-    plain_steps = 50
-    t_plain = 0.0
-    for w in sample:
-        with D.Simulation(w, precision=D.DIRAC_C128, stream=stream.cuda_stream) as s:
-            s.set_state(w.psi0)
-            s.step(3, w.dt)
+    try:
+        def run(n_steps, tune=False):
+            slots = []
+            for s, w in zip(sims, ws):
+                s.set_state(w.psi0)
+                slots.append(D.dirac_batch_submit(batch, s.ctx, n_steps, w.dt))
             torch.cuda.synchronize()
+            if tune:  # CTA shapes of every class timed on its contexts (outside the timing)
+                D.dirac_batch_autotune(batch, 5)
+            if world > 1:
+                torch.distributed.barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            s.step(plain_steps, w.dt)
+            ticks = 0
+            while D.dirac_batch_active(batch):
+                D.dirac_batch_run(batch, 1)
+                ticks += 1
             e1.record(stream)
+            D.dirac_batch_synchronize(batch)
             torch.cuda.synchronize()
-            t_plain += e0.elapsed_time(e1) * 1e-3 / plain_steps * sum(
-                x.points for x in ws if x.nx == w.nx) / w.points
-    plain = pts / t_plain
-    # the whole tick against HBM: every instance's step moves the same 88 B per point as a
-    # single grid's (all classes' launches, per replica)
-    peak, peak_kind = hbm_peak()
-    gbs = 88.0 * pts / (ms * 1e-3 / args.steps) / 1e9
-    batch_roofline = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                      "frac": gbs / peak, "traffic": None, "peak_source": peak_kind,
-                      "kernel": "whole tick (every class's x and y passes)",
-                      "algorithmic_bytes_per_point_step": 88}
+            for sl in slots:
+                D.dirac_batch_release(batch, sl)
+            return max_over_ranks(e0.elapsed_time(e1), world, device="cuda"), ticks
+
+        warm = max(3, args.warmup)
+        run(warm, tune=True)
+        shapes = {str(n): list(D.dirac_batch_launch_shape(batch, n, n)) for n in W.BATCH_SIZES
+                  if any(w.nx == n for w in ws)}
+        l0 = D.dirac_batch_launch_count(batch)
+        with Clocks(torch.cuda.current_device()) as clk:
+            ms, ticks = run(steps)
+        launches = int(D.dirac_batch_launch_count(batch) - l0)
+        value = whole_job_value(pts, steps, world, ms)
+        # plain complex128 path, each instance alone, one instance of each size, scaled by
+        # the mix's point counts
+        sample, seen = [], set()
+        for w in ws:
+            if w.nx not in seen:
+                seen.add(w.nx)
+                sample.append(w)
+        rates = {w.nx: plain_c128_rate(w, stream) for w in sample}
+        t_plain = sum(x.points / rates[x.nx] for x in ws)
+        plain = pts / t_plain
+        peak, peak_kind = hbm_peak()
+        gbs = 88.0 * pts / (ms * 1e-3 / steps) / 1e9
+        rec = {
+            "workload": f"batch-mix-{count}", "value": value, "unit": UNIT, "steps": steps,
+            "warmup": warm, "ms_per_step": ms / steps, "dtype": "f32",
+            "precision": "c64 batched, FP64 tables and reductions",
+            "sizes": {str(n): sum(1 for w in ws if w.nx == n) for n in W.BATCH_SIZES},
+            "points_per_step": pts, "steps_per_tick": args.tick, "ticks": ticks,
+            "gpu_launches": launches, "launches_per_tick": launches / max(1, ticks),
+            "autotuned_threads_xy": shapes,
+            "l2": "working set larger than L2 (no flush)",
+            "plain_c128_single_instance": {
+                "value": plain, "unit": UNIT,
+                "per_size": {str(k): v for k, v in sorted(rates.items())},
+                "sample": "one instance of each size alone, 50 steps, weighted by the mix's "
+                          "point counts"},
+            "batched_over_plain_c128": value / world / plain,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": "whole tick (every class's x and y passes)",
+                         "algorithmic_bytes_per_point_step": 88},
+            "clocks": clk.summary(),
+        }
+        if check:
+            rec["rel_l2_vs_oracle"] = batch_oracle_check(batch, sims, ws, sample, stream)
+        return rec
+    finally:
+        D.dirac_batch_destroy(batch)
+        for s in sims:
+            s.close()
+
+
+def batch_oracle_check(batch, sims, ws, sample, stream):
+    """Per size: one instance stepped in the batch (complex64) and alone in complex128,
+    both against the FP64 oracle after BATCH_CHECK_STEPS[n] steps."""
+    import torch
+
+    import oracle
+    import paper_1909_02894_gb300 as D
+
+    oracle.build()
+    idx = {w.nx: ws.index(w) for w in sample}
+    slots = {}
+    for n, i in idx.items():
+        sims[i].set_state(ws[i].psi0)
+        slots[n] = D.dirac_batch_submit(batch, sims[i].ctx, BATCH_CHECK_STEPS[n], ws[i].dt)
+    while D.dirac_batch_active(batch):
+        D.dirac_batch_run(batch, 1)
+    D.dirac_batch_synchronize(batch)
+    torch.cuda.synchronize()
+    out = {}
+    for n, i in sorted(idx.items()):
+        D.dirac_batch_release(batch, slots[n])
+        w, k = ws[i], BATCH_CHECK_STEPS[n]
+        got64 = sims[i].get_state()
+        with D.Simulation(w, precision=D.DIRAC_C128, stream=stream.cuda_stream) as s:
+            s.set_state(w.psi0)
+            s.step(k, w.dt)
+            got128 = s.get_state()
+        ref = oracle.run(oracle.Problem.from_workload(w), w.psi0, w.dt, k)
+        out[str(n)] = {"steps": k, "c64_batched": W.rel_l2(got64, ref),
+                       "c128_plain": W.rel_l2(got128, ref),
+                       "kept_norm": float(np.linalg.norm(ref) / np.linalg.norm(w.psi0))}
+    out["max_c64_batched"] = max(v["c64_batched"] for v in out.values())
+    return out
+
+
+def run_batch(args):
+    """The batch-mix record as a line of its own (--workload batch-mix): `--steps` steps
+    per instance (2000 in the configuration)."""
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:  # independent replicas of the whole mix, one per rank
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    rec = batch_record(args, stream, args.steps, world, check=(world == 1))
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch-mix-{count}", "precision": "c64 batched",
-                   "sizes": {str(n): sum(1 for w in ws if w.nx == n) for n in W.BATCH_SIZES},
-                   "points_per_step": pts, "steps_per_tick": args.tick,
-                   "autotuned_threads_xy": shapes,
-                   "l2": "working set larger than L2 (no flush)"},
-        "plain_c128_single_instance": {"value": plain, "unit": UNIT,
-                                       "sample": f"one instance of each size, {plain_steps} steps, "
-                                                 "scaled by the mix's point counts"},
-        "batched_over_plain_c128": value / world / plain,
-        "roofline": batch_roofline,
-        "clocks": clk.summary(),
-        "gpu_launches": int(D.dirac_batch_launch_count(batch) - l0),
+        "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": rec["warmup"], "ms_per_step": rec["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": rec["workload"], "precision": "c64 batched",
+                   "sizes": rec["sizes"], "points_per_step": rec["points_per_step"],
+                   "steps_per_tick": args.tick, "autotuned_threads_xy":
+                   rec["autotuned_threads_xy"], "l2": rec["l2"]},
+        "plain_c128_single_instance": rec["plain_c128_single_instance"],
+        "batched_over_plain_c128": rec["batched_over_plain_c128"],
+        "roofline": rec["roofline"], "clocks": rec["clocks"],
+        "gpu_launches": rec["gpu_launches"], "launches_per_tick": rec["launches_per_tick"],
     }
+    if "rel_l2_vs_oracle" in rec:
+        line["rel_l2_vs_oracle"] = rec["rel_l2_vs_oracle"]
     if rank == 0:
         print(json.dumps(line))
-    D.dirac_batch_destroy(batch)
-    for s in sims:
-        s.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
 
 
-def run_serve(args):
-    """Strained-graphene request stream through the continuous-batching loop: Poisson
-    arrivals at the configured rate (200/s) over a window of --serve-seconds, grids
-    {256,512,1024,2048}^2, steps U{500..5000}, complex64, 1% FP64-checked; and the same
-    stream at a sustainable rate. Reports p50/p99 latency and throughput."""
+def oracle_reference(max_n):
+    """A reference(workload, steps) callable for the serving check: the FP64 CPU oracle on
+    grids up to max_n^2 (None above, where the check falls back to the complex128 path)."""
+    import oracle
+
+    oracle.build()
+
+    def ref(w, steps):
+        if w.nx > max_n:
+            return None
+        return oracle.run(oracle.Problem.from_workload(w), w.psi0, w.dt, steps)
+    return ref
+
+
+def serve_record(args, stream, rate, window, check=True, plain_rates=None):
+    """The strained-graphene request stream through the continuous-batching loop: Poisson
+    arrivals at `rate` over `window` seconds, grids {256,512,1024,2048}^2, steps
+    U{500..5000}, complex64; latency p50/p99, throughput, clocks, and the FP64 check of 1%
+    of the requests (at least one)."""
     import torch
 
-    import paper_1909_02894_gb300 as D
     from paper_1909_02894_gb300 import serve as S
+
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    reqs = S.graphene_requests(rate=rate, duration=window, seed=1914)
+    if check and reqs and not any(r.check for r in reqs):
+        reqs[0].check = True
+    work = sum(r.nx * r.ny * r.steps for r in reqs)
+    srv = S.Server(budget, steps_per_tick=args.tick, stream=stream.cuda_stream)
+    try:
+        for r in reqs:
+            srv.submit(r)
+        with Clocks(torch.cuda.current_device()) as clk:
+            t0 = time.perf_counter()
+            results = srv.run(t0=t0)
+            elapsed = time.perf_counter() - t0
+    finally:
+        srv.close()
+    summ = S.latency_summary(results)
+    summ.update({"rate_per_s": rate, "window_s": window, "throughput": work / elapsed,
+                 "unit": UNIT, "elapsed_s": elapsed, "max_active": srv.max_active,
+                 "admitted_while_busy": srv.admitted_while_busy, "ticks": srv.ticks,
+                 "budget_bytes": budget, "clocks": clk.summary(), "dtype": "f32"})
+    if plain_rates:
+        # the same requests, each alone on the plain complex128 path
+        t_plain = sum(r.nx * r.ny * r.steps / plain_rates[r.nx] for r in reqs
+                      if r.nx in plain_rates)
+        summ["served_over_plain_c128"] = (t_plain / elapsed
+                                          if all(r.nx in plain_rates for r in reqs) else None)
+    if check:
+        checks = S.fp64_check(results, stream=stream.cuda_stream, short_steps=200,
+                              reference=oracle_reference(512))
+        summ["fp64_check"] = {
+            "requests": len(checks),
+            "max_short_rel_l2": max((c["short_rel_l2"] for c in checks), default=None),
+            "max_rel_l2": max((c["rel_l2"] for c in checks), default=None),
+            "max_err_vs_initial_norm": max((c["err_vs_initial_norm"] for c in checks),
+                                           default=None),
+            "min_kept_norm": min((c["kept_norm"] for c in checks), default=None),
+            "checks": [{k: c[k] for k in ("n", "steps", "rel_l2", "err_vs_initial_norm",
+                                          "kept_norm", "short_steps", "short_rel_l2",
+                                          "short_kept_norm", "short_reference")}
+                       for c in checks]}
+    return summ
+
+
+def run_serve(args):
+    """The serving record as a line of its own (--workload serve): the configured rate
+    (200/s) over --serve-seconds and a sustainable rate over --sustainable-seconds."""
+    import torch
 
     world, rank, local = dist_setup(args)
     if rank != 0:  # one request stream, served by rank 0's GPU; other ranks have no work
         return 0
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    free, total = torch.cuda.mem_get_info()
-    budget = int(0.8 * free)
-    out = {}
-    for label, rate, window in (("configured", 200.0, args.serve_seconds),
-                                ("sustainable", args.sustainable_rate, args.sustainable_seconds)):
-        reqs = S.graphene_requests(rate=rate, duration=window, seed=1914)
-        work = sum(r.nx * r.ny * r.steps for r in reqs)
-        srv = S.Server(budget, steps_per_tick=args.tick, stream=stream.cuda_stream)
-        for r in reqs:
-            srv.submit(r)
-        t0 = time.perf_counter()
-        results = srv.run(t0=t0)
-        elapsed = time.perf_counter() - t0
-        srv.close()
-        summ = S.latency_summary(results)
-        summ.update({"rate_per_s": rate, "window_s": window, "throughput": work / elapsed,
-                     "elapsed_s": elapsed, "max_active": srv.max_active,
-                     "admitted_while_busy": srv.admitted_while_busy, "ticks": srv.ticks})
-        checks = S.fp64_check(results, stream=stream.cuda_stream)
-        summ["fp64_check"] = {
-            "requests": len(checks),
-            "max_rel_l2": max((c["rel_l2"] for c in checks), default=None),
-            "max_err_vs_initial_norm": max((c["err_vs_initial_norm"] for c in checks),
-                                           default=None),
-            "min_kept_norm": min((c["kept_norm"] for c in checks), default=None),
-            "checks": [{k: c[k] for k in ("n", "steps", "rel_l2", "err_vs_initial_norm",
-                                          "kept_norm")} for c in checks]}
-        out[label] = summ
+    out = {"configured": serve_record(args, stream, 200.0, args.serve_seconds),
+           "sustainable": serve_record(args, stream, args.sustainable_rate,
+                                       args.sustainable_seconds)}
     line = {
         "metric": "p50/p99 solve ms and grid-point*steps/s (serving)",
         "value": out["configured"]["throughput"], "unit": UNIT, "n_gpus": 1,
@@ -416,11 +568,11 @@ def run_serve(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serve-graphene", "arrivals": "Poisson",
                    "sizes": list(W.SERVE_SIZES), "steps": [500, 5000],
-                   "budget_bytes": budget, "steps_per_tick": args.tick},
+                   "steps_per_tick": args.tick},
+        "clocks": out["configured"]["clocks"],
         "serving": out,
     }
-    if rank == 0:
-        print(json.dumps(line))
+    print(json.dumps(line))
     return 0
 
 
@@ -436,6 +588,14 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--tick", type=int, default=32)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--batch-steps", type=int, default=2000,
+                    help="steps per instance of the default line's batch-mix record")
+    ap.add_argument("--record-serve-seconds", type=float, default=0.5,
+                    help="arrival window of the default line's serving record")
+    ap.add_argument("--no-records", action="store_true",
+                    help="default line without its batch-mix and serving records")
+    ap.add_argument("--check-steps", type=int, default=5,
+                    help="steps of the default line's rel-L2 check against the oracle")
     ap.add_argument("--sustainable-rate", type=float, default=4.0)
     ap.add_argument("--sustainable-seconds", type=float, default=20.0)
     ap.add_argument("--scheme", default="printed",
@@ -533,6 +693,20 @@ def main():
         krylov = {"arnoldi_steps_per_step": iters / args.steps}
     traffic = None if (symmetric or poly or cn) else ncu_traffic(args.workload)
 
+    # ---- rel-L2 of the GPU result against the FP64 oracle (full grid, a few steps), and
+    # the oracle's own rate on the host cores from the same runs
+    check = None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        k = max(2, args.check_steps)
+        cpu, ref = cpu_baseline(w, scheme=args.scheme, degree=args.poly_degree, check_steps=k)
+        sim.set_state(w.psi0)
+        sim.step(k, w.dt)
+        got = sim.get_state()
+        check = {"value": W.rel_l2(got, ref), "steps": k, "grid": [w.nx, w.ny],
+                 "tolerance": 1e-5 if prec == D.DIRAC_C64 else 1e-11,
+                 "against": "FP64 CPU oracle, whole grid, same launch configuration"}
+
     # ---- end to end through the public API with pinned host buffers
     e2e = None
     if args.e2e_solves > 0:
@@ -548,11 +722,16 @@ def main():
             D.lib().dirac_get_state(sim.ctx, host_out.data_ptr(), 0)
         barrier()
         ms_e2e = max_over_ranks((time.perf_counter() - t0) * 1e3, world, device="cuda")
+        # each solve copies its initial state in and its final state out once; per time
+        # step that is the solve's bytes over its steps
         e2e = {"value": whole_job_value(pts, solve_steps * args.e2e_solves, world, ms_e2e),
                "unit": UNIT,
-               "h2d_bytes_per_step": host_in.numel() * 16,
-               "d2h_bytes_per_step": host_out.numel() * 16,
-               "step": f"one solve: set_state(host) + {solve_steps} steps + get_state(host)"}
+               "h2d_bytes_per_step": host_in.numel() * 16 / solve_steps,
+               "d2h_bytes_per_step": host_out.numel() * 16 / solve_steps,
+               "h2d_bytes_per_solve": host_in.numel() * 16,
+               "d2h_bytes_per_solve": host_out.numel() * 16,
+               "solves": args.e2e_solves, "steps_per_solve": solve_steps,
+               "solve": f"set_state(pinned host) + {solve_steps} steps + get_state(pinned host)"}
 
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
@@ -592,11 +771,31 @@ def main():
         }
         if krylov:
             line["krylov"] = krylov
-        if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, scheme=args.scheme,
-                                                degree=args.poly_degree)
-        print(json.dumps(line))
+        if check is not None:
+            line["rel_l2_vs_oracle"] = check
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
     sim.close()
+    if (rank == 0 and world == 1 and not args.no_records and args.scheme == "printed"
+            and args.workload == "large-4096"):
+        # the batched/served complex64 throughput against the plain complex128 path, each
+        # with its error against the FP64 oracle (a failure is recorded, not fatal)
+        try:
+            line["batch"] = batch_record(args, stream, args.batch_steps)
+        except Exception as e:  # noqa: BLE001
+            line["batch"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            rates = dict((int(k), v) for k, v in line["batch"].get(
+                "plain_c128_single_instance", {}).get("per_size", {}).items())
+            for n in W.SERVE_SIZES:
+                if n not in rates:
+                    rates[n] = plain_c128_rate(W.serve_instance(n, 100, 1), stream)
+            line["serving"] = serve_record(args, stream, 200.0, args.record_serve_seconds,
+                                           plain_rates=rates)
+        except Exception as e:  # noqa: BLE001
+            line["serving"] = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0:
+        print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0

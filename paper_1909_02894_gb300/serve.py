@@ -7,7 +7,8 @@ retired at once and their memory is freed for the next admissions. Latency is me
 from arrival to the moment the request's last step has completed on the device.
 
 A seeded subset of requests is checked after the run against the same simulation in
-complex128 (the FP64 path), reported as rel-L2.
+complex128 (the FP64 path), at full length and over a short horizon while the packet still
+holds its norm, reported as rel-L2.
 """
 from __future__ import annotations
 
@@ -151,12 +152,19 @@ def latency_summary(results: List[Result]):
             "max_ms": float(lat.max())}
 
 
-def fp64_check(results: List[Result], stream=None):
-    """Each checked complex64 result against the same run in complex128: rel-L2, and the
-    error relative to the initial norm with the fraction of the norm the absorbing layer
-    left. When the layer has removed nearly all of the wave packet (long requests), rel-L2
-    divides FP32 rounding of the absorbed part by a near-zero residual, so such a result is
-    judged by its error against the initial norm."""
+def fp64_check(results: List[Result], stream=None, short_steps: int = 200,
+               reference: Optional[Callable] = None):
+    """Each checked complex64 result against complex128 (the FP64 path).
+
+    Full length: the served state against the same request run in complex128 -- rel-L2,
+    the error relative to the initial norm, and the fraction of the norm the absorbing
+    layer left. When the layer has removed nearly all of the wave packet (long requests),
+    rel-L2 divides FP32 rounding of the absorbed part by a near-zero residual, so that
+    figure is judged by its error against the initial norm.
+    Short horizon: the same request over min(steps, short_steps) steps, while the packet
+    still holds its norm, in complex64 (alone, which equals the served computation bit for
+    bit) against `reference(workload, steps)` if given (e.g. the FP64 CPU oracle), else
+    the complex128 path: rel-L2 and the kept norm."""
     out = []
     for r in results:
         if r.workload is None or r.state is None:
@@ -169,6 +177,20 @@ def fp64_check(results: List[Result], stream=None):
         n0 = float(np.linalg.norm(w.psi0))
         kept = float(np.linalg.norm(ref)) / n0
         err0 = float(np.linalg.norm(r.state - ref)) / n0
+        k = min(r.steps, short_steps)
+        with Simulation(w, precision=DIRAC_C64, stream=stream) as s:
+            s.set_state(w.psi0)
+            s.step(k, w.dt)
+            got_k = s.get_state()
+        ref_k, ref_kind = (reference(w, k), "oracle") if reference is not None else (None, None)
+        if ref_k is None:
+            with Simulation(w, precision=DIRAC_C128, stream=stream) as s:
+                s.set_state(w.psi0)
+                s.step(k, w.dt)
+                ref_k, ref_kind = s.get_state(), "c128"
         out.append({"rid": r.rid, "n": r.nx, "steps": r.steps, "rel_l2": W.rel_l2(r.state, ref),
-                    "err_vs_initial_norm": err0, "kept_norm": kept})
+                    "err_vs_initial_norm": err0, "kept_norm": kept,
+                    "short_steps": k, "short_rel_l2": W.rel_l2(got_k, ref_k),
+                    "short_kept_norm": float(np.linalg.norm(ref_k)) / n0,
+                    "short_reference": ref_kind})
     return out

@@ -7,6 +7,7 @@ import pytest
 import oracle
 import paper_1909_02894_gb300 as D
 from paper_1909_02894_gb300 import workloads as W
+from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -137,7 +138,7 @@ def test_batch_matches_oracle_and_admits_late_arrivals():
         D.dirac_batch_release(batch, b)
         for w, s in ((w1, s1), (w2, s2)):
             ref = oracle.run(oracle.Problem.from_workload(w), w.psi0, w.dt, w.steps)
-            assert W.rel_l2(s.get_state(), ref) <= 1e-5
+            assert_parity(s.get_state(), ref, w, 1e-5)
         # the freed budget admits the third one in a reused slot
         c = D.dirac_batch_submit(batch, s3.ctx, 3, w2.dt)
         assert c in (a, b)

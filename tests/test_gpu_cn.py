@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_1909_02894_gb300 as D
 from paper_1909_02894_gb300 import workloads as W
+from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +48,7 @@ def test_plain_128_cn_matches_oracle(prec):
     steps = 100 if prec == D.DIRAC_C128 else 40
     ref = oracle_run(w, steps)
     got, iters = gpu_run(w, prec, steps)
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
     assert iters >= steps
 
 
@@ -57,7 +58,7 @@ def test_cn_curved_metric_layer_mass_split_calls(prec):
     w.mass = 0.3
     ref = oracle_run(w, 30)
     got, _ = gpu_run(w, prec, 30, calls=[5, 10, 15])
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -73,7 +74,7 @@ def test_cn_rectangular_grids(prec, nx, ny):
                    sigma0=0.5, theta=0.0, psi0=psi0, dt=0.05, steps=5)
     ref = oracle_run(w, 5)
     got, _ = gpu_run(w, prec, 5)
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
 
 
 def test_cn_conserves_the_norm_in_flat_space_with_a_short_restart():
@@ -88,7 +89,7 @@ def test_cn_conserves_the_norm_in_flat_space_with_a_short_restart():
     got, _ = gpu_run(w, D.DIRAC_C128, 10, restart=3)
     assert abs(np.linalg.norm(got) / np.linalg.norm(psi0) - 1.0) <= 1e-11
     ref = oracle_run(w, 10)
-    assert W.rel_l2(got, ref) <= 1e-11
+    assert_parity(got, ref, w, 1e-11)
 
 
 def test_cn_reports_non_convergence():

@@ -6,6 +6,7 @@ import pytest
 import oracle
 import paper_1909_02894_gb300 as D
 from paper_1909_02894_gb300 import workloads as W
+from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -36,18 +37,18 @@ def gpu_run(w, steps, scheme=D.DIRAC_SCHEME_II):
 def test_scheme_ii_complex_layer(ptype, theta):
     w = layer_workload(ptype, theta)
     ref = oracle.run(oracle.Problem.from_workload(w), w.psi0, w.dt, 60)
-    assert W.rel_l2(gpu_run(w, 60), ref) <= 1e-11
+    assert_parity(gpu_run(w, 60), ref, w, 1e-11)
 
 
 def test_other_schemes_complex_layer():
     w = layer_workload(1, 0.5, steps=20)
     prob = oracle.Problem.from_workload(w)
     ref = oracle.run(prob, w.psi0, w.dt, 20, scheme=oracle.SCHEME_II_SYMMETRIC)
-    assert W.rel_l2(gpu_run(w, 20, D.DIRAC_SCHEME_II_SYMMETRIC), ref) <= 1e-11
+    assert_parity(gpu_run(w, 20, D.DIRAC_SCHEME_II_SYMMETRIC), ref, w, 1e-11)
     ref = oracle.run_poly(prob, w.psi0, w.dt, 20, oracle.POLY_CHEBYSHEV, 8)
-    assert W.rel_l2(gpu_run(w, 20, D.DIRAC_SCHEME_POLY_CHEBYSHEV), ref) <= 1e-11
+    assert_parity(gpu_run(w, 20, D.DIRAC_SCHEME_POLY_CHEBYSHEV), ref, w, 1e-11)
     ref, _ = oracle.run_cn(prob, w.psi0, w.dt, 20, tol=1e-14)
-    assert W.rel_l2(gpu_run(w, 20, D.DIRAC_SCHEME_CRANK_NICOLSON), ref) <= 1e-11
+    assert_parity(gpu_run(w, 20, D.DIRAC_SCHEME_CRANK_NICOLSON), ref, w, 1e-11)
 
 
 def test_complex_layer_rectangular_and_long_lines():
@@ -61,4 +62,4 @@ def test_complex_layer_rectangular_and_long_lines():
                    c=1.0, pml_width_x=nx // 16, pml_width_y=ny // 8, pml_type=2, sigma0=0.5,
                    theta=0.7, psi0=psi0, dt=0.05, steps=5)
     ref = oracle.run(oracle.Problem.from_workload(w), psi0, w.dt, 5)
-    assert W.rel_l2(gpu_run(w, 5), ref) <= 1e-11
+    assert_parity(gpu_run(w, 5), ref, w, 1e-11)

@@ -9,6 +9,7 @@ import pytest
 import oracle
 import paper_1909_02894_gb300 as D
 from paper_1909_02894_gb300 import workloads as W
+from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +49,7 @@ def test_plain_128_poly_matches_oracle(prec, family, degree):
     w = W.plain_128()
     steps = 200
     ref = oracle_run(w, steps, family, degree)
-    assert W.rel_l2(gpu_run(w, prec, steps, family, degree), ref) <= TOL[prec]
+    assert_parity(gpu_run(w, prec, steps, family, degree), ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -60,7 +61,7 @@ def test_poly_curved_metric_layer_mass_split_calls(prec, family):
     w.mass = 0.3
     ref = oracle_run(w, 60, family, 8)
     got = gpu_run(w, prec, 60, family, 8, calls=(10, 20, 30))
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -75,7 +76,7 @@ def test_poly_rectangular_grids(prec, nx, ny):
                    pml_width_x=max(1, nx // 16), pml_width_y=max(1, ny // 16), pml_type=1,
                    sigma0=0.5, theta=0.0, psi0=psi0, dt=0.02, steps=5)
     ref = oracle_run(w, 5, "chebyshev", 8)
-    assert W.rel_l2(gpu_run(w, prec, 5, "chebyshev", 8), ref) <= TOL[prec]
+    assert_parity(gpu_run(w, prec, 5, "chebyshev", 8), ref, w, TOL[prec])
 
 
 def test_chebyshev_reaches_the_free_propagator_on_the_gpu():
@@ -96,7 +97,7 @@ def test_chebyshev_reaches_the_free_propagator_on_the_gpu():
     r1 = cs * h1 - 1j * sn * ((KX + 1j * KY) * h0)
     exact = np.stack([np.fft.ifft2(r0), np.fft.ifft2(r1)])
     got = gpu_run(w, D.DIRAC_C128, 10, "chebyshev", 24)
-    assert W.rel_l2(got, exact) <= 1e-11
+    assert_parity(got, exact, w, 1e-11)
 
 
 def test_poly_degree_validation_and_batch_guard():

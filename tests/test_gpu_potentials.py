@@ -9,6 +9,7 @@ import pytest
 import oracle
 import paper_1909_02894_gb300 as D
 from paper_1909_02894_gb300 import workloads as W
+from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +54,7 @@ def test_scheme_ii_with_potentials(prec, calls):
     w = W.graphene_strained(n=128, steps=200)
     w.mass = 0.3
     ref = oracle.run(oracle_problem(w), w.psi0, w.dt, 200)
-    assert W.rel_l2(gpu_run(w, prec, 200, calls=calls), ref) <= TOL[prec]
+    assert_parity(gpu_run(w, prec, 200, calls=calls), ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -61,7 +62,7 @@ def test_symmetric_order_with_potentials(prec):
     w = W.plain_128(steps=100)
     ref = oracle.run(oracle_problem(w), w.psi0, w.dt, 100, scheme=oracle.SCHEME_II_SYMMETRIC)
     got = gpu_run(w, prec, 100, scheme=D.DIRAC_SCHEME_II_SYMMETRIC)
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -69,10 +70,10 @@ def test_polynomial_and_cn_with_potentials(prec):
     w = W.plain_128(steps=30)
     ref = oracle.run_poly(oracle_problem(w), w.psi0, w.dt, 30, oracle.POLY_CHEBYSHEV, 8)
     got = gpu_run(w, prec, 30, scheme=D.DIRAC_SCHEME_POLY_CHEBYSHEV)
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
     ref, _ = oracle.run_cn(oracle_problem(w), w.psi0, w.dt, 30, tol=1e-14)
     got = gpu_run(w, prec, 30, scheme=D.DIRAC_SCHEME_CRANK_NICOLSON)
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
 
 
 def test_constant_scalar_potential_is_a_phase_on_the_gpu():
@@ -106,7 +107,7 @@ def test_potentials_can_be_removed_and_batches_refuse_them():
         D.dirac_set_potentials(s.ctx, None, None, None)
         s.set_state(w.psi0)
         s.step(10, w.dt)
-        assert W.rel_l2(s.get_state(), ref) <= 1e-11
+        assert_parity(s.get_state(), ref, w, 1e-11)
         with pytest.raises(D.DiracError):
             D.dirac_set_potentials(s.ctx, np.full((w.ny, w.nx), np.nan), None, None)
 

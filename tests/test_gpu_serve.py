@@ -59,6 +59,7 @@ def test_fp64_check_of_served_requests():
     checks = S.fp64_check(results)
     assert len(checks) == len(reqs) > 0
     assert all(c["rel_l2"] <= 1e-5 for c in checks), checks
+    assert all(c["short_rel_l2"] <= 1e-5 and c["short_reference"] == "c128" for c in checks)
 
 
 def test_served_large_grids_equal_alone_runs():

@@ -11,6 +11,7 @@ import pytest
 import oracle
 import paper_1909_02894_gb300 as D
 from paper_1909_02894_gb300 import workloads as W
+from parity_util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +46,7 @@ def oracle_run(w, steps, psi0=None):
 def test_plain_128_symmetric_matches_oracle(prec, steps):
     w = W.plain_128()
     ref = oracle_run(w, steps)
-    assert W.rel_l2(gpu_run(w, prec, steps), ref) <= TOL[prec]
+    assert_parity(gpu_run(w, prec, steps), ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -60,7 +61,7 @@ def test_symmetric_split_into_several_calls(prec):
         for n in (20, 30, 50):
             s.step(n, w.dt)
         got = s.get_state()
-    assert W.rel_l2(got, ref) <= TOL[prec]
+    assert_parity(got, ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -81,21 +82,21 @@ def test_symmetric_every_line_length_and_aspect(prec, nx, ny):
                    pml_width_x=max(1, nx // 16), pml_width_y=max(1, ny // 16), pml_type=1,
                    sigma0=0.5, theta=0.0, psi0=psi0, dt=0.05, steps=5)
     ref = oracle_run(w, 5)
-    assert W.rel_l2(gpu_run(w, prec, 5), ref) <= TOL[prec]
+    assert_parity(gpu_run(w, prec, 5), ref, w, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
 def test_symmetric_strained_graphene_1024(prec):
     w = W.graphene_strained(n=1024, steps=6)
     ref = oracle_run(w, 6)
-    assert W.rel_l2(gpu_run(w, prec, 6), ref) <= TOL[prec]
+    assert_parity(gpu_run(w, prec, 6), ref, w, TOL[prec])
 
 
 def test_symmetric_large_4096_c64_vs_oracle():
     """The 4096^2 complex64 benchmark grid (persistent passes, both store layouts)."""
     w = W.large_4096(steps=2)
     ref = oracle_run(w, 2)
-    assert W.rel_l2(gpu_run(w, D.DIRAC_C64, 2), ref) <= TOL[D.DIRAC_C64]
+    assert_parity(gpu_run(w, D.DIRAC_C64, 2), ref, w, TOL[D.DIRAC_C64])
 
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
@@ -134,7 +135,7 @@ def test_scheme_switch_and_batch_guard():
         D.dirac_set_scheme(s.ctx, D.DIRAC_SCHEME_II)
         s.set_state(w.psi0)
         s.step(10, w.dt)
-        assert W.rel_l2(s.get_state(), ref) <= 1e-11
+        assert_parity(s.get_state(), ref, w, 1e-11)
         D.dirac_set_scheme(s.ctx, SYM)
         b = D.dirac_batch_create(1 << 30, D.DIRAC_C128, 8, None)
         try:
