@@ -225,6 +225,12 @@ dirac_status dirac_autotune(dirac_ctx *ctx, int reps, int *threads_x, int *threa
  * other launch shapes. */
 dirac_status dirac_test_timeout_next_step(dirac_ctx *ctx);
 
+/* Host-side fault injection for failure-detection tests (no GPU fault involved): with the
+ * environment variable DIRAC_FAULT=alloc:N (N >= 1) set when dirac_create runs, the N-th
+ * device allocation of that context fails as if the device were out of memory; the call
+ * frees everything it had allocated and returns DIRAC_ENOMEM, and later contexts (created
+ * without the variable) are unaffected. Any other value, or none, disables it. */
+
 /* Number of kernel launches this context has enqueued so far (for accounting). */
 long dirac_launch_count(const dirac_ctx *ctx);
 

@@ -59,6 +59,10 @@ struct dirac_ctx {
   bool state_set = false;
   int threads_x = 0, threads_y = 0;
   unsigned test_timeout_next = 0;  // test hook: next dirac_step's waits run out
+  // Host-side fault injection (DIRAC_FAULT=alloc:N at creation): the N-th device
+  // allocation of this context fails as if the device were out of memory; 0 = off.
+  int fault_alloc_at = 0;
+  int n_allocs = 0;
   long launches = 0;
   std::string err;
   std::vector<void*> allocs;

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <complex>
 #include <cstring>
 #include <new>
@@ -46,7 +47,23 @@ static dirac_status cuda_fail(dirac_ctx* c, cudaError_t e, const char* where) {
 
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
+// Failure-detection test hook read at creation: DIRAC_FAULT=alloc:N (N >= 1) makes the
+// N-th device allocation of the new context fail with cudaErrorMemoryAllocation, so the
+// creation returns DIRAC_ENOMEM after freeing what it had allocated. Anything else: off.
+static int fault_alloc_from_env() {
+  const char* f = getenv("DIRAC_FAULT");
+  if (!f || strncmp(f, "alloc:", 6) != 0) return 0;
+  char* end = nullptr;
+  const long n = strtol(f + 6, &end, 10);
+  return (end && *end == '\0' && n >= 1 && n < (1L << 30)) ? (int)n : 0;
+}
+
 static cudaError_t dalloc(dirac_ctx* ctx, void** p, size_t bytes) {
+  if (ctx->fault_alloc_at > 0 && ++ctx->n_allocs == ctx->fault_alloc_at) {
+    // injected failure: nothing is allocated, the caller unwinds as for a real one
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e == cudaSuccess) ctx->allocs.push_back(*p);
   return e;
@@ -851,6 +868,7 @@ dirac_status dirac_create(const dirac_grid* grid, const dirac_domain* domain,
   ctx->conn = conn;
   ctx->abs = ab;
   ctx->u_identity = (mass == 0.0 && conn == DIRAC_CONN_NONE);
+  ctx->fault_alloc_at = fault_alloc_from_env();
   cudaGetDevice(&ctx->device);
   if (cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
