@@ -97,6 +97,26 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def batch_traffic(count, pts):
+    """DRAM bytes per step of the whole batch mix from the committed ncu summary of one
+    tick, if it was taken on the current kernel sources and the same mix; else None."""
+    p = os.path.join(ROOT, "profiles", "batch_tick_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if (kv.get("kernel_hash") != kernel_hash() or kv.get("instances") != str(count)
+            or kv.get("points_per_step") != str(pts)):
+        return None
+    try:
+        return float(kv["dram_bytes_per_step"])
+    except (KeyError, ValueError):
+        return None
+
+
 def ncu_traffic(workload_name):
     """DRAM bytes per launch of the line pass from the committed ncu summary, if it was
     taken on the current kernel source; else None."""
@@ -163,6 +183,40 @@ class Clocks:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(rows)}
+
+
+class ProfileRegion:
+    """cudaProfilerStart/Stop around a timed region when --profile-region is given, so an
+    `ncu --profile-from-start off` capture covers exactly the timed launches."""
+
+    def __init__(self, on):
+        self.on = on
+
+    def __enter__(self):
+        if self.on:
+            import torch
+
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStart()
+        return self
+
+    def __exit__(self, *a):
+        if self.on:
+            import torch
+
+            torch.cuda.synchronize()
+            torch.cuda.cudart().cudaProfilerStop()
+
+
+def alu_peaks():
+    """Measured FMA throughput of the device (TFLOP/s): FP64, FP32, packed FP32 pairs."""
+    import paper_1909_02894_gb300 as D
+
+    return {"fp64_tflops": D.dirac_measure_alu_peak(D.ALU_FP64),
+            "fp32_tflops": D.dirac_measure_alu_peak(D.ALU_FP32),
+            "fp32x2_tflops": D.dirac_measure_alu_peak(D.ALU_FP32X2),
+            "how": "dirac_measure_alu_peak: 8 x 256-thread blocks per SM, 8 independent FMA "
+                   "chains per thread, CUDA events over one >= 2 ms launch after a warm-up"}
 
 
 def dist_setup(args):
@@ -366,7 +420,8 @@ def batch_record(args, stream, steps, world=1, check=True):
         shapes = {str(n): list(D.dirac_batch_launch_shape(batch, n, n)) for n in W.BATCH_SIZES
                   if any(w.nx == n for w in ws)}
         l0 = D.dirac_batch_launch_count(batch)
-        with Clocks(torch.cuda.current_device()) as clk:
+        with Clocks(torch.cuda.current_device()) as clk, \
+                ProfileRegion(getattr(args, "profile_region", False)):
             ms, ticks = run(steps)
         launches = int(D.dirac_batch_launch_count(batch) - l0)
         value = whole_job_value(pts, steps, world, ms)
@@ -398,9 +453,11 @@ def batch_record(args, stream, steps, world=1, check=True):
                           "point counts"},
             "batched_over_plain_c128": value / world / plain,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                         "frac": gbs / peak, "traffic": None, "peak_source": peak_kind,
+                         "frac": gbs / peak, "traffic": batch_traffic(count, pts),
+                         "peak_source": peak_kind,
                          "kernel": "whole tick (every class's x and y passes)",
-                         "algorithmic_bytes_per_point_step": 88},
+                         "algorithmic_bytes_per_point_step": 88,
+                         "traffic_unit": "DRAM bytes per step of the whole mix"},
             "clocks": clk.summary(),
         }
         if check:
@@ -594,6 +651,9 @@ def main():
                     help="arrival window of the default line's serving record")
     ap.add_argument("--no-records", action="store_true",
                     help="default line without its batch-mix and serving records")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="cudaProfilerStart/Stop around the timed region (for ncu "
+                         "--profile-from-start off)")
     ap.add_argument("--check-steps", type=int, default=5,
                     help="steps of the default line's rel-L2 check against the oracle")
     ap.add_argument("--sustainable-rate", type=float, default=4.0)
@@ -663,7 +723,7 @@ def main():
     it0 = D.dirac_krylov_iterations(sim.ctx)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
+    with Clocks(local) as clk, ProfileRegion(args.profile_region):
         barrier()
         ev0.record(stream)
         sim.step(args.steps, w.dt)
@@ -738,13 +798,17 @@ def main():
                 "kernel": "whole step (derivative passes, transposes, combines)"
                 if (poly or cn) else kernel_name(w, prec_name),
                 "algorithmic_bytes_per_point_step": bytes_pt}
+    peaks = alu_peaks() if rank == 0 else None
     if prec == D.DIRAC_C128 and not (poly or cn):
-        # FP64-bound: algorithmic flops per launch over the average launch duration
+        # FP64-bound: algorithmic flops per launch over the average launch duration, against
+        # the FP64 FMA rate measured on this device
         fl_pt = fft_flops_per_point_step(w.nx, w.ny)
         tflops = fl_pt * pts / float(passes) / per_launch_s / 1e12
-        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "nominal FP64 (2 FMA per SM per clock, 152 SMs, 2.07 GHz)",
+        p64 = peaks["fp64_tflops"] if peaks else FP64_PEAK_TFLOPS
+        roofline = {"bound": "alu", "achieved": tflops, "peak": p64,
+                    "unit": "TFLOP/s", "frac": tflops / p64, "traffic": None,
+                    "peak_source": "measured FP64 FMA rate (dirac_measure_alu_peak)" if peaks
+                    else "nominal FP64 (2 FMA per SM per clock, 152 SMs, 2.07 GHz)",
                     "kernel": kernel_name(w, prec_name),
                     "algorithmic_flops_per_point_step": fl_pt,
                     "hbm_frac": achieved / peak}
@@ -768,6 +832,7 @@ def main():
             "clocks": clk.summary(),
             "gpu_launches": int(launches),
             "e2e": e2e,
+            "alu_peaks": peaks,
         }
         if krylov:
             line["krylov"] = krylov

@@ -218,11 +218,12 @@ dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_
  * The state must be set; synchronises the stream. */
 dirac_status dirac_autotune(dirac_ctx *ctx, int reps, int *threads_x, int *threads_y);
 
-/* Test hook for failure detection: in the next dirac_step, the persistent pass's
- * bulk-copy waits expect 16 bytes that never arrive, so each wait runs out after its
- * bound (about 1.5 s), the kernel returns early and the next synchronising call reports
- * DIRAC_ETIMEOUT; the context stays usable (set the state again). No effect on the
- * other launch shapes. */
+/* Test hook for failure detection: in the next dirac_step -- or, for a context submitted
+ * to a batch, in the first tick that steps it -- the persistent pass's bulk-copy waits
+ * expect 16 bytes that never arrive, so each wait runs out after its bound (about 1.5 s),
+ * the kernel returns early and the next synchronising call (dirac_synchronize, or
+ * dirac_batch_poll / dirac_batch_synchronize) reports DIRAC_ETIMEOUT; the context stays
+ * usable (set the state again). No effect on the other launch shapes. */
 dirac_status dirac_test_timeout_next_step(dirac_ctx *ctx);
 
 /* Host-side fault injection for failure-detection tests (no GPU fault involved): with the
@@ -262,14 +263,17 @@ dirac_status dirac_batch_submit(dirac_batch *batch, dirac_ctx *inst, long n_step
 dirac_status dirac_batch_run(dirac_batch *batch, int n_ticks);
 
 /* *done = 1 once every step of the slot's context has finished on the device.
- * DIRAC_ETIMEOUT if a bounded device wait ran out. */
+ * DIRAC_ETIMEOUT if a bounded device wait ran out in a batched pass: every context in the
+ * batch at that moment is then marked failed (its state is not valid), stops stepping,
+ * and its poll keeps returning DIRAC_ETIMEOUT until it is released; the batch itself keeps
+ * working for contexts submitted afterwards (set their state again first). */
 dirac_status dirac_batch_poll(dirac_batch *batch, int slot, int *done);
 
 /* Returns the slot (and its budget); a context still running is cancelled after the
  * steps already enqueued. The context is the caller's again. */
 dirac_status dirac_batch_release(dirac_batch *batch, int slot);
 
-/* Waits for all enqueued ticks; DIRAC_ETIMEOUT as for dirac_synchronize. */
+/* Waits for all enqueued ticks; DIRAC_ETIMEOUT as for dirac_batch_poll. */
 dirac_status dirac_batch_synchronize(dirac_batch *batch);
 
 /* Number of contexts still stepping. */
@@ -320,6 +324,16 @@ void dirac_batch_destroy(dirac_batch *batch);
  * leaves that error in place for its owner. */
 dirac_status dirac_norms_noalloc(const double *psi, const double *weight, int nx, int ny,
                                  double ax, double ay, double *out, void *cuda_stream);
+
+/* Measurement helper (no counterpart in the paper): the device's fused multiply-add
+ * throughput, the denominator of the ALU-bound rooflines of the benchmark. kind 0: FP64
+ * FMA, 1: FP32 FMA, 2: FP32 packed pairs (two FMAs per fma.rn.f32x2 instruction).
+ * Launches eight 256-thread blocks per SM, each thread running eight independent FMA
+ * chains, on cuda_stream (NULL = the default stream), timed with CUDA events over one
+ * launch of at least 2 ms after a warm-up; *tflops receives 2 x FMAs / s / 1e12.
+ * Synchronises the stream; allocates nothing. DIRAC_EINVAL for another kind or a NULL
+ * tflops (message in dirac_last_error(NULL)), DIRAC_ECUDA if a launch fails. */
+dirac_status dirac_measure_alu_peak(int kind, double *tflops, void *cuda_stream);
 
 #ifdef __cplusplus
 }

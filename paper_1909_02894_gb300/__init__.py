@@ -39,7 +39,7 @@ ABI_SYMBOLS = (
     "dirac_batch_create", "dirac_batch_submit", "dirac_batch_run", "dirac_batch_poll",
     "dirac_batch_release", "dirac_batch_synchronize", "dirac_batch_active",
     "dirac_batch_launch_count", "dirac_batch_last_error", "dirac_batch_destroy",
-    "dirac_batch_autotune", "dirac_batch_launch_shape",
+    "dirac_batch_autotune", "dirac_batch_launch_shape", "dirac_measure_alu_peak",
 )
 
 
@@ -117,6 +117,8 @@ def lib():
         L.dirac_test_timeout_next_step.restype = C.c_int
         L.dirac_autotune.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
         L.dirac_autotune.restype = C.c_int
+        L.dirac_measure_alu_peak.argtypes = [i, dp, vp]
+        L.dirac_measure_alu_peak.restype = C.c_int
         L.dirac_footprint_bytes.argtypes = [C.POINTER(_Grid), i]
         L.dirac_footprint_bytes.restype = C.c_size_t
         L.dirac_batch_create.argtypes = [C.c_size_t, i, vp, i, C.POINTER(vp)]
@@ -298,6 +300,16 @@ def dirac_norms_noalloc(psi, weight, ax: float, ay: float, out, stream=None):
                                          None if weight is None else weight.data_ptr(), nx,
                                          ny, float(ax), float(ay), out.data_ptr(), stream),
                None)
+
+
+ALU_FP64, ALU_FP32, ALU_FP32X2 = 0, 1, 2
+
+
+def dirac_measure_alu_peak(kind: int, stream=None) -> float:
+    """Measured FMA throughput in TFLOP/s (kind: ALU_FP64, ALU_FP32, ALU_FP32X2)."""
+    t = C.c_double(0.0)
+    _check(lib().dirac_measure_alu_peak(int(kind), C.byref(t), stream), None)
+    return t.value
 
 
 def dirac_test_timeout_next_step(ctx):

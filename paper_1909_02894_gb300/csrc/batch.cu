@@ -51,6 +51,7 @@ struct Slot {
   long total = 0;
   double dt = 0.0;
   bool started = false;
+  bool failed = false;  // a bounded device wait ran out while it was in the batch
   int state = 0;  // 0 free, 1 active, 2 finished (until released)
   unsigned long long finish_tick = 0;
 };
@@ -137,6 +138,27 @@ static dirac_status grow_class(dirac_batch* b, Class& c, int need) {
 
 // Fill the host tables of a class for one tick; returns the number of steps any of its
 // contexts takes in this tick.
+// Reads the device error flag (after the work it covers has completed). A bounded wait
+// that ran out leaves every context then in the batch without a valid state: they are
+// marked failed and stop stepping (poll reports DIRAC_ETIMEOUT until they are released),
+// and the flag is cleared so that contexts submitted afterwards step normally.
+static dirac_status batch_device_error(dirac_batch* b, const char* where) {
+  int flag = 0;
+  BCK(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+  if (!flag) return DIRAC_OK;
+  BCK(cudaMemset(b->d_err, 0, sizeof(int)), "error flag");
+  for (Slot& sl : b->slots) {
+    if (sl.state == 0) continue;
+    sl.failed = true;
+    if (sl.state == 1) {
+      sl.left = 0;
+      sl.state = 2;
+      sl.finish_tick = b->ticks ? b->ticks : 1;
+    }
+  }
+  return bfail(b, DIRAC_ETIMEOUT, where);
+}
+
 template <typename T>
 static int fill_class(dirac_batch* b, Class& c, int K) {
   std::vector<int>& m = c.members;
@@ -149,7 +171,7 @@ static int fill_class(dirac_batch* b, Class& c, int K) {
     for (int s : m) {
       const Slot& sl = b->slots[s];
       if (sl.left <= k) break;
-      const dirac_ctx* x = sl.ctx;
+      dirac_ctx* x = sl.ctx;
       InstPtrs<T>& px = tab[((size_t)k * 2 + 0) * c.capacity + cnt];
       InstPtrs<T>& py = tab[((size_t)k * 2 + 1) * c.capacity + cnt];
       px.in = (const Q4<T>*)x->psi;
@@ -165,6 +187,11 @@ static int fill_class(dirac_batch* b, Class& c, int K) {
       py.u_store = x->u_identity ? nullptr
                                  : (const Q4<T>*)(k + 1 == sl.left ? x->u_t : x->u2_t);
       py.mult = (const Q4<T>*)x->mult_y;
+      // failure-detection test hook (dirac_test_timeout_next_step): the first x pass of
+      // the context in this tick waits for bytes that never arrive
+      px.test_extra_tx = k == 0 ? x->test_timeout_next : 0u;
+      py.test_extra_tx = 0u;
+      if (k == 0) x->test_timeout_next = 0;
       ++cnt;
     }
     c.h_count[k] = cnt;
@@ -508,12 +535,17 @@ dirac_status dirac_batch_poll(dirac_batch* b, int slot, int* done) {
   const Slot& sl = b->slots[slot];
   *done = 0;
   if (sl.state != 2) return DIRAC_OK;
-  cudaError_t e = cudaEventQuery(b->tick_events[sl.finish_tick - 1]);
-  if (e == cudaErrorNotReady) return DIRAC_OK;
-  if (e != cudaSuccess) return bfail(b, DIRAC_ECUDA, cudaGetErrorString(e));
-  int flag = 0;
-  BCK(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
-  if (flag) return bfail(b, DIRAC_ETIMEOUT, "a bounded device wait ran out in a batched pass");
+  if (sl.finish_tick >= 1 && sl.finish_tick <= b->tick_events.size()) {
+    cudaError_t e = cudaEventQuery(b->tick_events[sl.finish_tick - 1]);
+    if (e == cudaErrorNotReady) return DIRAC_OK;
+    if (e != cudaSuccess) return bfail(b, DIRAC_ECUDA, cudaGetErrorString(e));
+  }
+  if (sl.failed)
+    return bfail(b, DIRAC_ETIMEOUT, "a bounded device wait ran out while this context was "
+                                    "in the batch; its state is not valid");
+  dirac_status st = batch_device_error(b, "a bounded device wait ran out in a batched pass; "
+                                          "the contexts in the batch have no valid state");
+  if (st != DIRAC_OK) return st;
   *done = 1;
   return DIRAC_OK;
 }
@@ -541,10 +573,8 @@ dirac_status dirac_batch_release(dirac_batch* b, int slot) {
 dirac_status dirac_batch_synchronize(dirac_batch* b) {
   if (!b) return DIRAC_EINVAL;
   BCK(cudaStreamSynchronize(b->stream), "synchronize");
-  int flag = 0;
-  BCK(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
-  if (flag) return bfail(b, DIRAC_ETIMEOUT, "a bounded device wait ran out in a batched pass");
-  return DIRAC_OK;
+  return batch_device_error(b, "a bounded device wait ran out in a batched pass; the "
+                               "contexts in the batch have no valid state");
 }
 
 int dirac_batch_active(const dirac_batch* b) {
@@ -568,9 +598,10 @@ dirac_status dirac_batch_autotune(dirac_batch* b, int reps) {
                                            : autotune_class<double>(b, kv.second, reps, &changed);
     if (st != DIRAC_OK) return st;
   }
-  int flag = 0;
-  BCK(cudaMemcpy(&flag, b->d_err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
-  if (flag) return bfail(b, DIRAC_ETIMEOUT, "a bounded device wait ran out in a timed pass");
+  {
+    dirac_status st = batch_device_error(b, "a bounded device wait ran out in a timed pass");
+    if (st != DIRAC_OK) return st;
+  }
   if (changed && b->graph) {  // the next tick captures a graph with the new shapes
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;

@@ -44,6 +44,7 @@ struct InstPtrs {
   const Q4<T>* u_load;
   const Q4<T>* u_store;
   const Q4<T>* mult;
+  unsigned test_extra_tx;  // test hook of this instance (see LinePassArgs); 0 normally
 };
 
 template <typename T>
@@ -81,6 +82,7 @@ __device__ __forceinline__ void bind_instance(LinePassArgs<T>& a, int k) {
   a.u_load = p.u_load;
   a.u_store = p.u_store;
   a.mult = p.mult;
+  a.test_extra_tx = p.test_extra_tx;
 }
 
 // Read-only cached loads of the table types.

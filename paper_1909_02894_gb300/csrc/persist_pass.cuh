@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(1024, 1)
     size_t first;
     const LinePassArgs<T> x = args_of(grp, &first);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&bars[0], GROUP_BYTES + a0.test_extra_tx);
+    mbar_arrive_expect_tx(&bars[0], GROUP_BYTES + x.test_extra_tx);
     bulk_copy_g2s(psi_z, x.in + first, GROUP_BYTES, &bars[0]);
   };
   auto issue_bu = [&](int grp) {  // thread 0; an empty request completes its phase at once
