@@ -391,7 +391,7 @@ def batch_record(args, stream, steps, world=1, check=True):
                                  stream=stream.cuda_stream)
     pts = sum(w.points for w in ws)
     try:
-        def run(n_steps, tune=False):
+        def run(n_steps, tune=False, profile=False):
             slots = []
             for s, w in zip(sims, ws):
                 s.set_state(w.psi0)
@@ -403,13 +403,14 @@ def batch_record(args, stream, steps, world=1, check=True):
                 torch.distributed.barrier()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ticks = 0
-            while D.dirac_batch_active(batch):
-                D.dirac_batch_run(batch, 1)
-                ticks += 1
-            e1.record(stream)
-            D.dirac_batch_synchronize(batch)
+            with ProfileRegion(profile):
+                e0.record(stream)
+                ticks = 0
+                while D.dirac_batch_active(batch):
+                    D.dirac_batch_run(batch, 1)
+                    ticks += 1
+                e1.record(stream)
+                D.dirac_batch_synchronize(batch)
             torch.cuda.synchronize()
             for sl in slots:
                 D.dirac_batch_release(batch, sl)
@@ -420,9 +421,8 @@ def batch_record(args, stream, steps, world=1, check=True):
         shapes = {str(n): list(D.dirac_batch_launch_shape(batch, n, n)) for n in W.BATCH_SIZES
                   if any(w.nx == n for w in ws)}
         l0 = D.dirac_batch_launch_count(batch)
-        with Clocks(torch.cuda.current_device()) as clk, \
-                ProfileRegion(getattr(args, "profile_region", False)):
-            ms, ticks = run(steps)
+        with Clocks(torch.cuda.current_device()) as clk:
+            ms, ticks = run(steps, profile=getattr(args, "profile_region", False))
         launches = int(D.dirac_batch_launch_count(batch) - l0)
         value = whole_job_value(pts, steps, world, ms)
         # plain complex128 path, each instance alone, one instance of each size, scaled by

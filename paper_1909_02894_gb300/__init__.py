@@ -14,7 +14,9 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdirac.so")
+# DIRAC_LIB may name another build of the same library (e.g. one made with other
+# DIRAC_NVCC_EXTRA flags); by default the in-tree libdirac.so.
+LIB_PATH = os.environ.get("DIRAC_LIB") or os.path.join(HERE, "libdirac.so")
 
 DIRAC_OK, DIRAC_EINVAL, DIRAC_ENOMEM, DIRAC_EUNSUPPORTED = 0, 1, 2, 3
 DIRAC_ECUDA, DIRAC_ETIMEOUT, DIRAC_ENONFINITE, DIRAC_ESTATE = 4, 5, 6, 7

@@ -28,10 +28,20 @@ def _deps():
             [os.path.join(HERE, "..", "include", "dirac.h"), __file__])
 
 
+def _extra_flags():
+    """Extra nvcc flags from DIRAC_NVCC_EXTRA (e.g. "-DDGB_PACKED_F32X2=0"), split on
+    whitespace; a change of them forces a rebuild."""
+    return os.environ.get("DIRAC_NVCC_EXTRA", "").split()
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     newest = max(os.path.getmtime(p) for p in _deps())
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
+    extra = _extra_flags()
+    stamp = LIB + ".flags"
+    old_extra = open(stamp).read() if os.path.exists(stamp) else ""
+    if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest
+            and old_extra == " ".join(extra)):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
@@ -40,7 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in sources:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -55,6 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
+    with open(stamp, "w") as f:
+        f.write(" ".join(extra))
     return LIB
 
 

@@ -31,6 +31,73 @@ template <typename T>
 __device__ __forceinline__ Cx<T> cmulc(Cx<T> a, Cx<T> b) {
   return {a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im};
 }
+// ---- packed FP32 pairs (sm_100 and later): the (re, im) of a complex64 value in one
+// 64-bit register pair, two FP32 operations per instruction, each rounded exactly like its
+// scalar counterpart (add/sub/fma.rn.f32x2).
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long add_f32x2(unsigned long long a,
+                                                         unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long sub_f32x2(unsigned long long a,
+                                                         unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// a * b + c per lane
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a,
+                                                         unsigned long long b,
+                                                         unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long pk2(Cx<float> a) { return pk2(a.re, a.im); }
+__device__ __forceinline__ Cx<float> upk2(unsigned long long r) {
+  Cx<float> a;
+  upk2(r, a.re, a.im);
+  return a;
+}
+
+// a + b and a - b: one packed instruction for complex64, the scalar pair otherwise.
+// Building with -DDGB_PACKED_F32X2=0 keeps the scalar form for complex64 too (same results).
+#ifndef DGB_PACKED_F32X2
+#define DGB_PACKED_F32X2 1
+#endif
+template <typename T>
+__device__ __forceinline__ Cx<T> cadd_p(Cx<T> a, Cx<T> b) { return cadd(a, b); }
+template <typename T>
+__device__ __forceinline__ Cx<T> csub_p(Cx<T> a, Cx<T> b) { return csub(a, b); }
+// s * a + b with the same real s on both parts (a single fma.rn.f32x2 for complex64)
+template <typename T>
+__device__ __forceinline__ Cx<T> cfma_p(T s, Cx<T> a, Cx<T> b) {
+  return {s * a.re + b.re, s * a.im + b.im};
+}
+#if DGB_PACKED_F32X2
+template <>
+__device__ __forceinline__ Cx<float> cadd_p<float>(Cx<float> a, Cx<float> b) {
+  return upk2(add_f32x2(pk2(a), pk2(b)));
+}
+template <>
+__device__ __forceinline__ Cx<float> csub_p<float>(Cx<float> a, Cx<float> b) {
+  return upk2(sub_f32x2(pk2(a), pk2(b)));
+}
+template <>
+__device__ __forceinline__ Cx<float> cfma_p<float>(float s, Cx<float> a, Cx<float> b) {
+  return upk2(fma_f32x2(pk2(s, s), pk2(a), pk2(b)));
+}
+#endif
+
 template <typename T>
 __device__ __forceinline__ Cx<T> mul_i(Cx<T> a) { return {-a.im, a.re}; }
 template <typename T>

@@ -105,19 +105,23 @@ __device__ __forceinline__ Q4<double> ldg_q4(const Q4<double>* p) {
 }
 
 // ---------------------------------------------------------------- small DFTs
+// Complex additions whose operands need no swap of real and imaginary parts go through
+// cadd_p / csub_p: for complex64 one packed-pair instruction (add/sub.rn.f32x2) instead
+// of two, with identical results. Additions of a value times +-i keep the scalar form,
+// where the swap and sign fold into the operands.
 template <typename T, bool INV>
 __device__ __forceinline__ void dft2(Cx<T>& a, Cx<T>& b) {
   const Cx<T> t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+  a = cadd_p(t, b);
+  b = csub_p(t, b);
 }
 
 template <typename T, bool INV>
 __device__ __forceinline__ void dft4(Cx<T>& x0, Cx<T>& x1, Cx<T>& x2, Cx<T>& x3) {
-  const Cx<T> a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
+  const Cx<T> a = cadd_p(x0, x2), b = csub_p(x0, x2), c = cadd_p(x1, x3), d = csub_p(x1, x3);
   const Cx<T> jd = INV ? mul_i(d) : mul_mi(d);
-  x0 = cadd(a, c);
-  x2 = csub(a, c);
+  x0 = cadd_p(a, c);
+  x2 = csub_p(a, c);
   x1 = cadd(b, jd);
   x3 = csub(b, jd);
 }
@@ -146,10 +150,10 @@ __device__ __forceinline__ void dft8(Cx<T> (&x)[8]) {
   o1 = w16<T, INV, 2>(o1);
   o2 = w16<T, INV, 4>(o2);
   o3 = w16<T, INV, 6>(o3);
-  x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
-  x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
+  x[0] = cadd_p(e0, o0); x[4] = csub_p(e0, o0);
+  x[1] = cadd_p(e1, o1); x[5] = csub_p(e1, o1);
   x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
-  x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+  x[3] = cadd_p(e3, o3); x[7] = csub_p(e3, o3);
 }
 
 // Radix-16 butterfly with an optional input twiddle tw[(t - 1) step] on element t
@@ -500,12 +504,13 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       const Cx<T> oth = shfl_pair(v[m]);
       const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
       Cx<T> d;
-      if (c == 0) d = cadd(dp, dm);
-      else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+      if (c == 0) d = cadd_p(dp, dm);
+      else d = a.sigma == 0 ? csub_p(dp, dm) : mul_i(csub_p(dp, dm));
       Cx<T> p = in_c[2 * gi];
       if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
       const T bm1 = a.beta ? a.beta[gi] : T(0);
-      Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+      // (p + d) + (b - 1) d
+      Cx<T> o = cfma_p(bm1, d, cadd_p(p, d));
       if (a.beta_im) {  // complex b - 1: add i Im(b - 1) d
         const T bi = a.beta_im[gi];
         o = {o.re - bi * d.im, o.im + bi * d.re};

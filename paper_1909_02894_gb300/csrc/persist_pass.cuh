@@ -265,7 +265,7 @@ __device__ __forceinline__ void dft2_lane(Cx<T> (&v)[8], bool hi) {
   for (int r = 0; r < 8; ++r) {
     const Cx<T> p = {__shfl_xor_sync(0xffffffffu, v[r].re, 2),
                      __shfl_xor_sync(0xffffffffu, v[r].im, 2)};
-    v[r] = hi ? csub(p, v[r]) : cadd(v[r], p);
+    v[r] = cfma_p(hi ? T(-1) : T(1), v[r], p);  // p - v or v + p, exactly
   }
 }
 
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(1024, 1)
             Q4<T> p = psi_z[i];
             if (a.u_load) p = apply_u(u_z[PG::upos(i)], p);
             pp[h] = p;
-            if (a.sigma == 0) v[m] = {p.x + sg * p.z, p.y + sg * p.w};
+            if (a.sigma == 0) v[m] = cfma_p(sg, Cx<T>{p.z, p.w}, Cx<T>{p.x, p.y});
             else v[m] = {p.x + sg * p.w, p.y - sg * p.z};
           }
           const Q4<T> mine = c ? pp[1] : pp[0];
@@ -638,11 +638,19 @@ __global__ void __launch_bounds__(1024, 1)
             const int i = j + (4 * c + mm) * J;
             const Q4<T> dd = stage[PG::spos(i)];  // (D+, D-)
             const Cx<T> dp = {dd.x, dd.y}, dm = {dd.z, dd.w};
-            const Cx<T> d1 = cadd(dp, dm);
-            const Cx<T> d2 = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+            const Cx<T> d1 = cadd_p(dp, dm);
+            const Cx<T> dd2 = csub_p(dp, dm);
             const T bm1 = a.beta ? beta_z[PG::bpos(i)] : T(0);
-            Q4<T> o = {(pk[4 * mm] + d1.re) + bm1 * d1.re, (pk[4 * mm + 1] + d1.im) + bm1 * d1.im,
-                       (pk[4 * mm + 2] + d2.re) + bm1 * d2.re, (pk[4 * mm + 3] + d2.im) + bm1 * d2.im};
+            // psi + D + (b - 1) D per component
+            const Cx<T> o1 = cfma_p(bm1, d1, cadd_p(Cx<T>{pk[4 * mm], pk[4 * mm + 1]}, d1));
+            Cx<T> o2;
+            if (a.sigma == 0) {
+              o2 = cfma_p(bm1, dd2, cadd_p(Cx<T>{pk[4 * mm + 2], pk[4 * mm + 3]}, dd2));
+            } else {
+              const Cx<T> d2 = mul_i(dd2);
+              o2 = {(pk[4 * mm + 2] + d2.re) + bm1 * d2.re, (pk[4 * mm + 3] + d2.im) + bm1 * d2.im};
+            }
+            Q4<T> o = {o1.re, o1.im, o2.re, o2.im};
             if (a.u_store) o = apply_u(u_z[PG::upos(i)], o);
             stage[PG::spos(i)] = o;
           }
@@ -660,11 +668,11 @@ __global__ void __launch_bounds__(1024, 1)
               const Cx<T> oth = shfl_pair(v[m]);
               const Cx<T> dp = c ? oth : v[m], dm = c ? v[m] : oth;
               Cx<T> d;
-              if (c == 0) d = cadd(dp, dm);
-              else d = a.sigma == 0 ? csub(dp, dm) : mul_i(csub(dp, dm));
+              if (c == 0) d = cadd_p(dp, dm);
+              else d = a.sigma == 0 ? csub_p(dp, dm) : mul_i(csub_p(dp, dm));
               const Cx<T> p = {pk[2 * mm], pk[2 * mm + 1]};
               const T bm1 = a.beta ? beta_z[lrow + i] : T(0);
-              Cx<T> o = {(p.re + d.re) + bm1 * d.re, (p.im + d.im) + bm1 * d.im};
+              Cx<T> o = cfma_p(bm1, d, cadd_p(p, d));  // (p + d) + (b - 1) d
               if (a.u_store) o = apply_u_row(u_z[lrow + i], o, shfl_pair(o), c);
               my_stage[2 * i] = o;
             }
