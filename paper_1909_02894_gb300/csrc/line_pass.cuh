@@ -69,6 +69,13 @@ struct LinePassArgs {
                             // makes the persistent pass's bounded wait run out
   int store_normal;         // 0 = out is [L][n_lines] (transposed store), 1 = out is
                             // [n_lines][L] like `in` (out must not alias in)
+  // Batched tick launch (the persistent pass runs every step of a tick in one launch):
+  // inst is then the tick's table [tick_k steps][2 passes][inst_capacity], n_inst the
+  // active count per step; work items are taken from *tick_queue (zero at launch) and
+  // tick_done[i] counts the finished line groups of instance slot i (zero at launch).
+  int tick_k;
+  int* tick_queue;
+  int* tick_done;
 };
 
 // Batched launches: a block (or group) of lines belongs to instance `k`; take that

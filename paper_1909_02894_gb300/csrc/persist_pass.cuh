@@ -99,8 +99,16 @@ struct PGeo {
   static_assert(BETA_PITCH % 16 == 0 && U_PITCH % 16 == 0 && OFF_BAR % 16 == 0, "bulk copy");
   // positions in the padded staging buffer / b - 1 zone / U zone of point i of a line
   static __device__ __forceinline__ int spos(int i) { return SWAP ? i + i / PAD_EVERY : i; }
-  static __device__ __forceinline__ int bpos(int i) { return SWAP ? i + 4 * (i / PAD_EVERY) : i; }
-  static __device__ __forceinline__ int upos(int i) { return SWAP ? i + i / PAD_EVERY : i; }
+  // The same for point j + m L/E with 0 <= j < L/E: in the padded 4096-point layout
+  // L/E = PAD_EVERY, so that point's padding is m slots (no division at run time).
+  static __device__ __forceinline__ int spos_jm(int j, int m) {
+    return SWAP ? j + m * (L / E + 1) : j + m * (L / E);
+  }
+  static __device__ __forceinline__ int bpos_jm(int j, int m) {
+    return SWAP ? j + m * (L / E + 4) : j + m * (L / E);
+  }
+  static __device__ __forceinline__ int upos_jm(int j, int m) { return spos_jm(j, m); }
+  static_assert(!SWAP || L / E == PAD_EVERY, "padding every L/E points");
 };
 
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
@@ -346,7 +354,8 @@ __global__ void __launch_bounds__(1024, 1)
   Q4<T>* psi_z = reinterpret_cast<Q4<T>*>(psmem + PG::OFF_PSI);
   T* beta_z = reinterpret_cast<T*>(psmem + PG::OFF_BETA);
   Q4<T>* u_z = reinterpret_cast<Q4<T>*>(psmem + PG::OFF_U);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::OFF_BAR);  // [0] spinor, [1] b-1/U
+  // [0] spinor copy, [1] b-1/U copy
+  uint64_t* bars = reinterpret_cast<uint64_t*>(psmem + PG::OFF_BAR);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(psmem + PG::OFF_BAR + 2 * sizeof(uint64_t));
   Cx<T>* t3tab = reinterpret_cast<Cx<T>*>(psmem + PG::OFF_T3);
   Cx<T>* t2tab = reinterpret_cast<Cx<T>*>(psmem + PG::OFF_T2);
@@ -480,6 +489,16 @@ __global__ void __launch_bounds__(1024, 1)
     issue_bu(cluster_id * CS + rank);
   }
 
+  // transposed store: this thread's line within an output segment (THREADS is a multiple
+  // of GL) and, for clusters, the shared::cluster address of that line in its owner's
+  // staging buffer
+  const int gline = tid % GL;
+  uint32_t gsrc = 0;
+  if constexpr (CS > 1) {
+    const int owner = gline / LPI;
+    gsrc = mapa_shared(smem_u32(psmem), (uint32_t)owner) +
+           (uint32_t)((gline - owner * LPI) * PG::SPITCH * sizeof(Q4<T>));
+  }
   bool failed = false;  // uniform across the CTA
   // copies requested / phases waited for, per mbarrier (uniform; at most one outstanding)
   const uint32_t first_issue = cluster_id < n_super ? 1u : 0u;
@@ -516,7 +535,7 @@ __global__ void __launch_bounds__(1024, 1)
             const int m = mm + h * (E / 2);
             const int i = j + m * J;
             Q4<T> p = psi_z[i];
-            if (a.u_load) p = apply_u(u_z[PG::upos(i)], p);
+            if (a.u_load) p = apply_u(u_z[PG::upos_jm(j, m)], p);
             pp[h] = p;
             if (a.sigma == 0) v[m] = cfma_p(sg, Cx<T>{p.z, p.w}, Cx<T>{p.x, p.y});
             else v[m] = {p.x + sg * p.w, p.y - sg * p.z};
@@ -548,7 +567,10 @@ __global__ void __launch_bounds__(1024, 1)
         }
         tmem_st16(tpark, park);
       }
-      // the spinor zone has been read: request the next group's rows
+      // The spinor zone has been read: every warp reports it on mbarrier 3, and thread 0
+      // requests the next group's rows once all have (no CTA-wide barrier here). A wait
+      // that ran out is folded into the CTA-wide check after the inverse FFT; until then
+      // the FFT runs on whatever the zone held.
       if (__syncthreads_or(!ok)) {
         failed = true;
         if (tid == 0) atomicExch(err, kErrTimeout);
@@ -628,19 +650,19 @@ __global__ void __launch_bounds__(1024, 1)
           // the neighbouring lane); thread c then finishes points m = 4c .. 4c + 3
           Cx<T>* stc = reinterpret_cast<Cx<T>*>(stage) + c;
 #pragma unroll
-          for (int m = 0; m < E; ++m) stc[2 * PG::spos(j + m * J)] = v[m];
+          for (int m = 0; m < E; ++m) stc[2 * PG::spos_jm(j, m)] = v[m];
           __syncwarp();
           float pk[2 * E];
           tmem_ld16(tpark, pk);
           tmem_wait_ld_regs(pk);
 #pragma unroll
           for (int mm = 0; mm < E / 2; ++mm) {
-            const int i = j + (4 * c + mm) * J;
-            const Q4<T> dd = stage[PG::spos(i)];  // (D+, D-)
+            const int m4 = 4 * c + mm;  // point j + m4 J
+            const Q4<T> dd = stage[PG::spos_jm(j, m4)];  // (D+, D-)
             const Cx<T> dp = {dd.x, dd.y}, dm = {dd.z, dd.w};
             const Cx<T> d1 = cadd_p(dp, dm);
             const Cx<T> dd2 = csub_p(dp, dm);
-            const T bm1 = a.beta ? beta_z[PG::bpos(i)] : T(0);
+            const T bm1 = a.beta ? beta_z[PG::bpos_jm(j, m4)] : T(0);
             // psi + D + (b - 1) D per component
             const Cx<T> o1 = cfma_p(bm1, d1, cadd_p(Cx<T>{pk[4 * mm], pk[4 * mm + 1]}, d1));
             Cx<T> o2;
@@ -651,8 +673,8 @@ __global__ void __launch_bounds__(1024, 1)
               o2 = {(pk[4 * mm + 2] + d2.re) + bm1 * d2.re, (pk[4 * mm + 3] + d2.im) + bm1 * d2.im};
             }
             Q4<T> o = {o1.re, o1.im, o2.re, o2.im};
-            if (a.u_store) o = apply_u(u_z[PG::upos(i)], o);
-            stage[PG::spos(i)] = o;
+            if (a.u_store) o = apply_u(u_z[PG::upos_jm(j, m4)], o);
+            stage[PG::spos_jm(j, m4)] = o;
           }
         } else {
           Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * PG::SPITCH) + c;
@@ -701,38 +723,44 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
       for (int q = 0; q < NIT; ++q) {
         const int idx = tid + q * PG::THREADS;
-        const int l = idx / L, i = idx - l * L;
-        a.out[gfirst + idx] = stage[(size_t)l * PG::SPITCH + PG::spos(i)];
+        if constexpr (PG::SWAP) {  // one line; the padding of idx is idx / PAD_EVERY
+          a.out[gfirst + idx] =
+              stage[tid + tid / PG::PAD_EVERY + q * (PG::THREADS + PG::THREADS / PG::PAD_EVERY)];
+        } else {
+          const int l = idx / L, i = idx - l * L;
+          a.out[gfirst + idx] = stage[(size_t)l * PG::SPITCH + PG::spos(i)];
+        }
       }
     } else if (!failed) {
       const Q4<T>* stage = reinterpret_cast<const Q4<T>*>(psmem);
       const int line0 = (int)(gfirst / L) - rank * LPI;
       const int i0 = rank * (L / CS);
       constexpr int NIT = (L / CS) * GL / PG::THREADS;
+      // item q of this thread: line gg of the segment, row i0 + tid / GL + q RPI
+      constexpr int RPI = PG::THREADS / GL;
+      static_assert(PG::THREADS % GL == 0, "items per row");
+      static_assert(!PG::SWAP || (RPI == PG::PAD_EVERY && (L / CS) % PG::PAD_EVERY == 0),
+                    "the padding of row i0 + tid / GL + q RPI is i0 / PAD_EVERY + q");
+      const int r0 = i0 + tid / GL;
+      const int sp0 = PG::SWAP ? r0 + i0 / PG::PAD_EVERY : r0;  // staging slot of row r0
+      constexpr int SPQ = PG::SWAP ? RPI + 1 : RPI;
       Q4<T> val[NIT];
       if constexpr (CS > 1) {
-        // gather through distributed shared memory: 32-bit shared::cluster addresses
-        const uint32_t local = smem_u32(stage);
+        // gather through distributed shared memory from the owner's staged line
 #pragma unroll
-        for (int q = 0; q < NIT; ++q) {
-          const int itm = tid + q * PG::THREADS;
-          const int gg = itm % GL, owner = gg / LPI;
-          const uint32_t off = (uint32_t)(((gg - owner * LPI) * PG::SPITCH + PG::spos(i0 + itm / GL)) *
-                                          sizeof(Q4<T>));
-          val[q] = ld_dsmem_q4<T>(mapa_shared(local, owner) + off);
-        }
+        for (int q = 0; q < NIT; ++q)
+          val[q] = ld_dsmem_q4<T>(gsrc + (uint32_t)((sp0 + q * SPQ) * sizeof(Q4<T>)));
       } else {
 #pragma unroll
-        for (int q = 0; q < NIT; ++q) {
-          const int itm = tid + q * PG::THREADS;
-          val[q] = stage[(size_t)(itm % GL) * PG::SPITCH + PG::spos(i0 + itm / GL)];
-        }
+        for (int q = 0; q < NIT; ++q)
+          val[q] = stage[(size_t)gline * PG::SPITCH + sp0 + q * SPQ];
       }
+      Q4<T>* dst = a.out + (size_t)r0 * a.n_lines + line0 + gline;
+      const size_t dstep = (size_t)RPI * a.n_lines;
 #pragma unroll
-      for (int q = 0; q < NIT; ++q) {
-        const int itm = tid + q * PG::THREADS;
-        a.out[(size_t)(i0 + itm / GL) * a.n_lines + line0 + itm % GL] = val[q];
-      }
+      for (int q = 0; q < NIT; ++q)  // streaming stores: the next pass reads them once
+        __stcs(reinterpret_cast<float4*>(dst + q * dstep),
+               make_float4(val[q].x, val[q].y, val[q].z, val[q].w));
     }
     // the staging buffer is free for the next super-group once every CTA of the cluster
     // has read it (the loads have returned: the stores above consumed them), so the
