@@ -208,11 +208,17 @@ long dirac_krylov_iterations(const dirac_ctx *ctx);
  * (complex64: persistent for lines of 1024 points or more, the smaller shape for
  * 256-point lines, else the larger;
  * complex128: the smaller shape for 1024-point lines, else the larger). Lines of 128
- * points or fewer and 4096-point lines have one shape only. Used by the autotuner.
- * DIRAC_EINVAL for other values. */
+ * points or fewer and 4096-point lines have one shape only. 256 or 512 plus
+ * DIRAC_LAUNCH_ALT_RADIX selects the other radix schedule of the FFT passes, where the line
+ * length has one: complex64 lines of 256..4096 points in radix-16 instead of radix-8
+ * passes, complex128 lines of 256..2048 points in radix-8 instead of radix-16 passes, each
+ * with its own lines-per-CTA pair (about 256 | 512 threads); elsewhere the flag is ignored.
+ * Used by the autotuner. DIRAC_EINVAL for other values. */
+#define DIRAC_LAUNCH_ALT_RADIX 0x10000
 dirac_status dirac_set_launch(dirac_ctx *ctx, int threads_x_pass, int threads_y_pass);
 
-/* Autotuner: times every CTA shape of the x and the y pass (reps launches each, CUDA
+/* Autotuner: times every CTA shape and radix schedule of the x and the y pass (the
+ * dirac_set_launch values; reps launches each, CUDA
  * events on the context's stream, output to scratch memory so the state is unchanged),
  * applies the fastest with dirac_set_launch and returns it in *threads_x, *threads_y.
  * The state must be set; synchronises the stream. */
@@ -241,9 +247,14 @@ size_t dirac_footprint_bytes(const dirac_grid *grid, dirac_precision precision);
 
 /* ---- Batched stepping of many independent contexts (any mix of grid sizes).
  * Contexts of the same grid size form a class; one tick advances every active context
- * by up to steps_per_tick steps, each step being, per class, one x-pass and one y-pass
- * launch over all of that class's active contexts, with the classes on parallel branches
- * of a CUDA graph captured once per class layout and replayed. Each context computes
+ * by up to steps_per_tick steps. A class of square complex64 grids with 256..2048-point
+ * lines whose passes run the persistent pass (the default) takes its whole tick in ONE
+ * persistent launch: work items (step, pass, context, line group) come from a queue, and
+ * each waits -- bounded, DIRAC_ETIMEOUT when the bound runs out -- until the context's
+ * previous pass is finished. Other classes launch, per step, one x-pass and one y-pass
+ * over all their active contexts (also when the environment variable DIRAC_BATCH_TICK=0 is
+ * set at dirac_batch_create). The classes run on parallel branches of a CUDA graph
+ * captured once per class layout and replayed. Each context computes
  * exactly what dirac_step(ctx, n_steps, dt) computes (Sec. 5.2 Scheme II); a submitted
  * context belongs to the batch until it is released and must not be stepped, read or
  * destroyed meanwhile. Contexts must have the batch's precision. */
@@ -291,7 +302,8 @@ long dirac_batch_launch_count(const dirac_batch *batch);
  * reps < 1, DIRAC_ETIMEOUT if a bounded device wait ran out. */
 dirac_status dirac_batch_autotune(dirac_batch *batch, int reps);
 
-/* The CTA shapes, in dirac_set_launch terms (256, 512, 1024 threads), that the class of
+/* The CTA shapes, in dirac_set_launch terms (256, 512, 1024 threads, possibly with
+ * DIRAC_LAUNCH_ALT_RADIX), that the class of
  * nx x ny contexts runs in this batch: the autotuner's choice, else the batch default
  * (complex64 lines of 256 points or more: the persistent pass; otherwise 512).
  * DIRAC_EINVAL if the batch has no such class. */

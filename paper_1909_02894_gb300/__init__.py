@@ -29,6 +29,8 @@ DIRAC_CONN_COVARIANT, DIRAC_CONN_PAPER_2D, DIRAC_CONN_NONE = 0, 1, 2
 DIRAC_SCHEME_II, DIRAC_SCHEME_II_SYMMETRIC = 0, 1
 DIRAC_SCHEME_POLY_TAYLOR, DIRAC_SCHEME_POLY_CHEBYSHEV = 2, 3
 DIRAC_SCHEME_CRANK_NICOLSON = 4
+# dirac_set_launch flag: the other radix schedule of the FFT passes (with 256 or 512)
+DIRAC_LAUNCH_ALT_RADIX = 0x10000
 
 # Every symbol the header declares; the CPU tests check that the library exports them.
 ABI_SYMBOLS = (

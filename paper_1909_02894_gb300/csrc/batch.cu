@@ -1,10 +1,12 @@
 // Batched stepping of many independent simulations (contexts) of uneven sizes.
 //
 // Contexts of the same grid size and precision form a class. One tick advances every
-// active context by up to K steps: for each step and class, one x-pass and one y-pass
-// launch cover all of that class's active contexts through a device table of
-// per-instance pointers, and the classes run on parallel branches of a CUDA graph so
-// that their work overlaps on the device. The graph of a tick is captured once per
+// active context by up to K steps through a device table of per-instance pointers
+// [K steps][2 passes][capacity]. A class of square complex64 grids whose passes run the
+// persistent pass takes the whole tick in one persistent launch (work items with
+// per-instance dependencies, line_pass_persistent's TICK mode); other classes launch, for
+// each step, one x-pass and one y-pass over all their active contexts. The classes run on
+// parallel branches of a CUDA graph so that their work overlaps on the device. The graph of a tick is captured once per
 // class layout (classes present and their table capacities) and replayed; between
 // ticks only the tables and the active counts (device memory) change, so contexts are
 // admitted and retired without re-capturing. Within a step, contexts are ordered by
@@ -17,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <new>
 #include <string>
@@ -42,7 +45,10 @@ struct Class {
   cudaStream_t stream = nullptr;
   void* tw_x = nullptr;  // twiddle tables owned by the class (contexts come and go)
   void* tw_y = nullptr;
+  void* tw_x_alt = nullptr;  // the same for the alternative radix schedule (if any)
+  void* tw_y_alt = nullptr;
   int opt[2] = {-1, -1};  // CTA shape of the x / y pass chosen by the autotuner (-1: default)
+  int* d_sync = nullptr;  // batched tick launch: per-slot done counters [capacity], queue
 };
 
 struct Slot {
@@ -75,6 +81,7 @@ struct dirac_batch {
   unsigned long long ticks = 0, ticks_done_seen = 0;
   int* d_err = nullptr;
   long launches = 0;
+  bool tick_launch = true;  // DIRAC_BATCH_TICK=0: per-step launches for every class
   std::string err;
 };
 
@@ -109,6 +116,9 @@ static void free_class(Class& c) {
   if (c.stream) cudaStreamDestroy(c.stream);
   if (c.tw_x) cudaFree(c.tw_x);
   if (c.tw_y) cudaFree(c.tw_y);
+  if (c.tw_x_alt) cudaFree(c.tw_x_alt);
+  if (c.tw_y_alt) cudaFree(c.tw_y_alt);
+  if (c.d_sync) cudaFree(c.d_sync);
   c = Class();
 }
 
@@ -117,21 +127,24 @@ static dirac_status grow_class(dirac_batch* b, Class& c, int need) {
   int cap = c.capacity ? c.capacity : 4;
   while (cap < need) cap *= 2;
   void *h = nullptr, *d = nullptr;
-  int *hc = nullptr, *dc = nullptr;
+  int *hc = nullptr, *dc = nullptr, *ds = nullptr;
   BCK(cudaMallocHost(&h, tab_bytes(b, cap)), "batch tables");
   BCK(cudaMalloc(&d, tab_bytes(b, cap)), "batch tables");
   BCK(cudaMallocHost((void**)&hc, b->steps_per_tick * sizeof(int)), "batch counts");
   BCK(cudaMalloc((void**)&dc, b->steps_per_tick * sizeof(int)), "batch counts");
+  BCK(cudaMalloc((void**)&ds, (cap + 1) * sizeof(int)), "batch tick counters");
   // the previous tables may still be read by an enqueued tick
   BCK(cudaStreamSynchronize(b->stream), "batch grow");
   if (c.h_tab) cudaFreeHost(c.h_tab);
   if (c.d_tab) cudaFree(c.d_tab);
   if (c.h_count) cudaFreeHost(c.h_count);
   if (c.d_count) cudaFree(c.d_count);
+  if (c.d_sync) cudaFree(c.d_sync);
   c.h_tab = h;
   c.d_tab = d;
   c.h_count = hc;
   c.d_count = dc;
+  c.d_sync = ds;
   c.capacity = cap;
   return DIRAC_OK;
 }
@@ -208,6 +221,7 @@ static dirac_status launch_class_step(dirac_batch* b, Class& c, int k, cudaStrea
     a.n_lines = pass == 0 ? c.ny : c.nx;
     a.sigma = pass;
     a.tw = (const Cx<T>*)(pass == 0 ? c.tw_x : c.tw_y);
+    a.tw_alt = (const Cx<T>*)(pass == 0 ? c.tw_x_alt : c.tw_y_alt);
     a.err = b->d_err;
     a.inst = (const InstPtrs<T>*)c.d_tab + ((size_t)k * 2 + pass) * c.capacity;
     a.n_inst = c.d_count + k;
@@ -219,6 +233,38 @@ static dirac_status launch_class_step(dirac_batch* b, Class& c, int k, cudaStrea
     BCK(launch_line_pass<T>(a, MODE_STEP, opt, st), "batched pass");
     b->launches += 1;
   }
+  return DIRAC_OK;
+}
+
+// A class whose passes both run the persistent pass on square complex64 grids of
+// 256..2048-point lines takes the whole tick in one persistent launch (work items with
+// per-instance dependencies); the others launch each step's x and y passes.
+template <typename T>
+static bool class_tick_launch(const dirac_batch* b, const Class& c) {
+  if (sizeof(T) != 4 || !b->tick_launch || c.nx != c.ny) return false;
+  if (c.nx < 256 || c.nx > 2048) return false;
+  for (int p = 0; p < 2; ++p)
+    if (c.opt[p] != -1 && c.opt[p] != 2) return false;
+  return true;
+}
+
+template <typename T>
+static dirac_status launch_class_tick(dirac_batch* b, Class& c, int K, cudaStream_t st) {
+  BCK(cudaMemsetAsync(c.d_sync, 0, (c.capacity + 1) * sizeof(int), st), "tick counters");
+  LinePassArgs<T> a{};
+  a.L = c.nx;
+  a.n_lines = c.ny;
+  a.sigma = 0;  // per work item
+  a.tw = (const Cx<T>*)c.tw_x;  // the same table serves both passes (nx == ny)
+  a.err = b->d_err;
+  a.inst = (const InstPtrs<T>*)c.d_tab;
+  a.n_inst = c.d_count;
+  a.inst_capacity = c.capacity;
+  a.tick_k = K;
+  a.tick_done = c.d_sync;
+  a.tick_queue = c.d_sync + c.capacity;
+  BCK(launch_line_pass_tick<T>(a, st), "batched tick");
+  b->launches += 1;
   return DIRAC_OK;
 }
 
@@ -242,8 +288,12 @@ static dirac_status tick_graph(dirac_batch* b, int K) {
     Class& c = kv.second;
     if (e != cudaSuccess || st != DIRAC_OK) break;
     e = cudaStreamWaitEvent(c.stream, b->fork, 0);
-    for (int k = 0; k < K && e == cudaSuccess && st == DIRAC_OK; ++k)
-      st = launch_class_step<T>(b, c, k, c.stream);
+    if (e == cudaSuccess && class_tick_launch<T>(b, c)) {
+      st = launch_class_tick<T>(b, c, K, c.stream);
+    } else {
+      for (int k = 0; k < K && e == cudaSuccess && st == DIRAC_OK; ++k)
+        st = launch_class_step<T>(b, c, k, c.stream);
+    }
     cudaEvent_t j = nullptr;
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(j, c.stream);
@@ -333,6 +383,10 @@ static std::vector<int> shape_candidates(int L) {
   if (L > 128 && L < 4096) o.push_back(0);
   o.push_back(1);
   if (sizeof(T) == 4 && L >= 256) o.push_back(2);
+  if (line_pass_radix_alt<T>(L)) {  // the other radix schedule (3 smaller, 4 larger CTA)
+    o.push_back(3);
+    if ((sizeof(T) == 4 && L < 4096) || (sizeof(T) == 8 && L < 2048)) o.push_back(4);
+  }
   return o;
 }
 
@@ -385,6 +439,7 @@ static dirac_status autotune_class(dirac_batch* b, Class& c, int reps, bool* cha
     a.n_lines = pass == 0 ? c.ny : c.nx;
     a.sigma = pass;
     a.tw = (const Cx<T>*)(pass == 0 ? c.tw_x : c.tw_y);
+    a.tw_alt = (const Cx<T>*)(pass == 0 ? c.tw_x_alt : c.tw_y_alt);
     a.err = b->d_err;
     a.inst = d_tab + (size_t)pass * n;
     a.n_inst = d_cnt;
@@ -431,6 +486,10 @@ dirac_status dirac_batch_create(size_t hbm_budget_bytes, dirac_precision precisi
   if (!b) return DIRAC_ENOMEM;
   b->prec = precision;
   b->budget = hbm_budget_bytes;
+  {
+    const char* t = getenv("DIRAC_BATCH_TICK");
+    b->tick_launch = !(t && t[0] == '0' && t[1] == '\0');
+  }
   b->steps_per_tick = steps_per_tick;
   cudaError_t e = cudaSuccess;
   if (cuda_stream) {
@@ -510,6 +569,17 @@ dirac_status dirac_batch_submit(dirac_batch* b, dirac_ctx* inst, long n_steps, d
     } else {
       BCK(launch_twiddles<double>(c.nx, line_pass_radix<double>(c.nx), (Cx<double>*)c.tw_x, b->stream), "twiddles");
       BCK(launch_twiddles<double>(c.ny, line_pass_radix<double>(c.ny), (Cx<double>*)c.tw_y, b->stream), "twiddles");
+    }
+    const int ax = b->prec == DIRAC_C64 ? line_pass_radix_alt<float>(c.nx) : line_pass_radix_alt<double>(c.nx);
+    const int ay = b->prec == DIRAC_C64 ? line_pass_radix_alt<float>(c.ny) : line_pass_radix_alt<double>(c.ny);
+    if (ax) BCK(cudaMalloc(&c.tw_x_alt, c.nx * cx), "class twiddles");
+    if (ay) BCK(cudaMalloc(&c.tw_y_alt, c.ny * cx), "class twiddles");
+    if (b->prec == DIRAC_C64) {
+      if (ax) BCK(launch_twiddles<float>(c.nx, ax, (Cx<float>*)c.tw_x_alt, b->stream), "twiddles");
+      if (ay) BCK(launch_twiddles<float>(c.ny, ay, (Cx<float>*)c.tw_y_alt, b->stream), "twiddles");
+    } else {
+      if (ax) BCK(launch_twiddles<double>(c.nx, ax, (Cx<double>*)c.tw_x_alt, b->stream), "twiddles");
+      if (ay) BCK(launch_twiddles<double>(c.ny, ay, (Cx<double>*)c.tw_y_alt, b->stream), "twiddles");
     }
     BCK(cudaStreamSynchronize(b->stream), "class twiddles");
   }
@@ -615,7 +685,8 @@ dirac_status dirac_batch_launch_shape(const dirac_batch* b, int nx, int ny, int*
   if (!b || !threads_x || !threads_y) return DIRAC_EINVAL;
   auto it = b->classes.find(std::make_pair(nx, ny));
   if (it == b->classes.end()) return DIRAC_EINVAL;
-  static const int th[3] = {256, 512, 1024};
+  static const int th[5] = {256, 512, 1024, 256 | DIRAC_LAUNCH_ALT_RADIX,
+                            512 | DIRAC_LAUNCH_ALT_RADIX};
   const int L[2] = {nx, ny};
   int* out[2] = {threads_x, threads_y};
   for (int p = 0; p < 2; ++p) {

@@ -28,6 +28,7 @@ struct dirac_ctx {
   void *beta1 = nullptr, *beta2T = nullptr;
   void *beta1_im = nullptr, *beta2T_im = nullptr;  // complex stretching: Im(b - 1)
   void *u_n = nullptr, *u_t = nullptr, *u2_t = nullptr;
+  void *tw_x_alt = nullptr, *tw_y_alt = nullptr;  // twiddles of the alternative radix
   void *tw_x = nullptr, *tw_y = nullptr, *mult_x = nullptr, *mult_y = nullptr,
        *dmult_x = nullptr, *dmult_y = nullptr;
   double* staging = nullptr;  // [2][ny][nx] complex128 for host transfers

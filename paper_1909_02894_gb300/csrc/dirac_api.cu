@@ -76,7 +76,14 @@ static void free_all(dirac_ctx* ctx) {
 
 // ------------------------------------------------------------------ precision dispatch
 // launch option for a pass from the dirac_set_launch preference (0 = default)
-static int pass_opt(const dirac_ctx* ctx, int threads, int L) {
+static int pass_opt(const dirac_ctx* ctx, int shape, int L) {
+  if (shape & DIRAC_LAUNCH_ALT_RADIX) {  // validated by dirac_set_launch
+    const int threads = shape & ~DIRAC_LAUNCH_ALT_RADIX;
+    if (ctx->prec == DIRAC_C64 ? line_pass_radix_alt<float>(L) : line_pass_radix_alt<double>(L))
+      return threads == 256 ? 3 : 4;
+    shape = threads;  // this line length has no alternative radix: the default one
+  }
+  const int threads = shape;
   if (threads == 256) return 0;
   if (threads == 512) return 1;
   if (threads == 1024) return 2;
@@ -109,6 +116,7 @@ static LinePassArgs<T> pass_args(dirac_ctx* ctx, int axis) {
   a.n_lines = axis == 0 ? ctx->ny : ctx->nx;
   a.sigma = axis;
   a.tw = (const Cx<T>*)(axis == 0 ? ctx->tw_x : ctx->tw_y);
+  a.tw_alt = (const Cx<T>*)(axis == 0 ? ctx->tw_x_alt : ctx->tw_y_alt);
   return a;
 }
 
@@ -635,6 +643,10 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
   }
   CK(dalloc(ctx, &ctx->tw_x, nx * sizeof(Cx<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->tw_y, ny * sizeof(Cx<T>)), "allocate tables");
+  if (line_pass_radix_alt<T>(nx))
+    CK(dalloc(ctx, &ctx->tw_x_alt, nx * sizeof(Cx<T>)), "allocate tables");
+  if (line_pass_radix_alt<T>(ny))
+    CK(dalloc(ctx, &ctx->tw_y_alt, ny * sizeof(Cx<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->mult_x, nx * sizeof(Q4<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->mult_y, ny * sizeof(Q4<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->dmult_x, nx * sizeof(Q4<T>)), "allocate tables");
@@ -710,6 +722,10 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
      "b - 1");
   CK(launch_twiddles<T>(nx, line_pass_radix<T>(nx), (Cx<T>*)ctx->tw_x, st), "twiddles");
   CK(launch_twiddles<T>(ny, line_pass_radix<T>(ny), (Cx<T>*)ctx->tw_y, st), "twiddles");
+  if (ctx->tw_x_alt)
+    CK(launch_twiddles<T>(nx, line_pass_radix_alt<T>(nx), (Cx<T>*)ctx->tw_x_alt, st), "twiddles");
+  if (ctx->tw_y_alt)
+    CK(launch_twiddles<T>(ny, line_pass_radix_alt<T>(ny), (Cx<T>*)ctx->tw_y_alt, st), "twiddles");
   CK(launch_deriv_mult<T>(nx, ctx->ax, (Q4<T>*)ctx->dmult_x, st), "derivative table");
   CK(launch_deriv_mult<T>(ny, ctx->ay, (Q4<T>*)ctx->dmult_y, st), "derivative table");
   ctx->launches += 7;
@@ -753,7 +769,8 @@ static dirac_status tune_pass(dirac_ctx* ctx, int axis, int reps, int* best, flo
   a.beta = (const T*)(axis == 0 ? ctx->beta1 : ctx->beta2T);
   a.u_store = (axis == 1 && !ctx->u_identity) ? (const Q4<T>*)ctx->u2_t : nullptr;
   const int L = a.L;
-  const int options[3] = {256, 512, 1024};
+  const int options[5] = {256, 512, 1024, 256 | DIRAC_LAUNCH_ALT_RADIX,
+                          512 | DIRAC_LAUNCH_ALT_RADIX};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0), "tune");
   CK(cudaEventCreate(&e1), "tune");
@@ -761,7 +778,8 @@ static dirac_status tune_pass(dirac_ctx* ctx, int axis, int reps, int* best, flo
   *best_ms = 1e30f;
   for (int t : options) {
     if (t == 1024 && !(sizeof(T) == 4 && L >= 256)) continue;  // persistent: complex64 only
-    const int opt = t == 256 ? 0 : t == 512 ? 1 : 2;
+    if ((t & DIRAC_LAUNCH_ALT_RADIX) && !line_pass_radix_alt<T>(L)) continue;
+    const int opt = pass_opt(ctx, t, L);
     cudaError_t e = cudaSuccess;
     for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch_line_pass<T>(a, MODE_STEP, opt, ctx->stream);
     if (e == cudaSuccess) e = cudaEventRecord(e0, ctx->stream);
@@ -1030,9 +1048,14 @@ long dirac_krylov_iterations(const dirac_ctx* ctx) { return ctx ? ctx->krylov_it
 dirac_status dirac_set_launch(dirac_ctx* ctx, int threads_x_pass, int threads_y_pass) {
   if (!ctx) return fail(nullptr, DIRAC_EINVAL, "ctx is NULL");
   const int t[2] = {threads_x_pass, threads_y_pass};
-  for (int k = 0; k < 2; ++k)
-    if (t[k] != 0 && t[k] != 256 && t[k] != 512 && t[k] != 1024)
-      return fail(ctx, DIRAC_EINVAL, "threads must be 0 (default), 256, 512 or 1024");
+  for (int k = 0; k < 2; ++k) {
+    const int th = t[k] & ~DIRAC_LAUNCH_ALT_RADIX;
+    const bool alt = (t[k] & DIRAC_LAUNCH_ALT_RADIX) != 0;
+    if ((th != 0 && th != 256 && th != 512 && th != 1024) || (alt && th != 256 && th != 512))
+      return fail(ctx, DIRAC_EINVAL,
+                  "shape must be 0 (default), 256, 512 or 1024, or 256 or 512 plus "
+                  "DIRAC_LAUNCH_ALT_RADIX");
+  }
   ctx->threads_x = threads_x_pass;
   ctx->threads_y = threads_y_pass;
   return DIRAC_OK;

@@ -18,10 +18,18 @@ void set_global_error(const std::string& msg);
 // variant (complex64 step mode, lines of 256..4096 points; otherwise as 1).
 template <typename T>
 cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st);
+// Every step of a batch tick of one class in one persistent launch (complex64, square
+// grids, 256..2048-point lines; cudaErrorInvalidValue otherwise).
+template <typename T>
+cudaError_t launch_line_pass_tick(const LinePassArgs<T>& a, cudaStream_t st);
 // Elements per thread (8 or 16) the line pass uses for line length L; the twiddle table
 // of that axis must be built for the same value.
 template <typename T>
 int line_pass_radix(int L);
+// The alternative radix schedule the autotuner may pick for lines of L points (0: none);
+// launch options 3 and 4 run it, with a twiddle table of that radix in tw_alt.
+template <typename T>
+int line_pass_radix_alt(int L);
 
 // ---- FP64 precompute (precompute.cu)
 // a1, a2, meff, w and the two log fields (packed as a complex128 spinor (f1, f2)) from the

@@ -12,10 +12,15 @@ namespace dgb {
 // spilling); shorter lines and FP64 use E = 16.
 template <typename T>
 constexpr int radix_e(int L) { return (sizeof(T) == 4 && L >= 256) ? 8 : 16; }
+// The other radix schedule the autotuner may choose (0: none): FP32 lines of 256..4096
+// points in radix-16 passes, FP64 lines of 256..2048 points in radix-8 passes.
+template <typename T>
+constexpr int radix_alt(int L) {
+  return L < 256 ? 0 : sizeof(T) == 4 ? (L <= 4096 ? 16 : 0) : (L <= 2048 ? 8 : 0);
+}
 
-template <typename T, int L, int LPC, int MODE>
+template <typename T, int L, int LPC, int MODE, int E = radix_e<T>(L)>
 static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
-  constexpr int E = radix_e<T>(L);
   using Gm = Geo<T, L, LPC, E>;
   if (a.n_lines % Gm::GL != 0 || a.n_lines < Gm::GL) return cudaErrorInvalidValue;
   auto kern = line_pass_kernel<T, L, LPC, E, MODE>;
@@ -145,9 +150,43 @@ static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st)
   return cudaLaunchKernelEx(&cfg, kern, a, groups, a.err);
 }
 
+// The alternative radix schedule (radix_alt), opt 3 the smaller and opt 4 the larger of two
+// CTA shapes (about 256 and 512 threads; 4096-point FP32 lines and 2048-point FP64 lines
+// have one, 512 threads). Its twiddle table (a.tw_alt) has the layout of that radix.
+template <typename T>
+static cudaError_t dispatch_alt(const LinePassArgs<T>& a0, int opt, cudaStream_t st) {
+  if (!a0.tw_alt) return cudaErrorInvalidValue;
+  LinePassArgs<T> a = a0;
+  a.tw = a0.tw_alt;
+  const bool big = opt == 4;
+  constexpr int M = MODE_STEP;
+  if constexpr (sizeof(T) == 4) {  // radix 16: 2 L / 16 threads per line
+    switch (a.L) {
+      case 256: return big ? launch_one<T, 256, 16, M, 16>(a, st) : launch_one<T, 256, 8, M, 16>(a, st);
+      case 512: return big ? launch_one<T, 512, 8, M, 16>(a, st) : launch_one<T, 512, 4, M, 16>(a, st);
+      case 1024: return big ? launch_one<T, 1024, 4, M, 16>(a, st) : launch_one<T, 1024, 2, M, 16>(a, st);
+      case 2048: return big ? launch_one<T, 2048, 2, M, 16>(a, st) : launch_one<T, 2048, 1, M, 16>(a, st);
+      case 4096: return launch_one<T, 4096, 1, M, 16>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  } else {  // radix 8: 2 L / 8 threads per line
+    switch (a.L) {
+      case 256: return big ? launch_one<T, 256, 8, M, 8>(a, st) : launch_one<T, 256, 4, M, 8>(a, st);
+      case 512: return big ? launch_one<T, 512, 4, M, 8>(a, st) : launch_one<T, 512, 2, M, 8>(a, st);
+      case 1024: return big ? launch_one<T, 1024, 2, M, 8>(a, st) : launch_one<T, 1024, 1, M, 8>(a, st);
+      case 2048: return launch_one<T, 2048, 1, M, 8>(a, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+}
+
 template <typename T>
 cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaStream_t st) {
   if (mode == MODE_DERIV) return dispatch<T, MODE_DERIV>(a, 0, st);
+  if (opt == 3 || opt == 4) {
+    if (radix_alt<T>(a.L) == 0) return cudaErrorInvalidValue;
+    return dispatch_alt<T>(a, opt, st);
+  }
   if constexpr (sizeof(T) == 4) {
     if (opt == 2) {
       switch (a.L) {
@@ -163,7 +202,61 @@ cudaError_t launch_line_pass(const LinePassArgs<T>& a, int mode, int opt, cudaSt
   return dispatch<T, MODE_STEP>(a, opt >= 1 ? 1 : 0, st);
 }
 
+// Batched tick launch (complex64, square grids, 256..2048-point lines): every step of
+// the tick in one persistent launch, one 1024-thread CTA per SM, work items from a
+// queue with per-instance dependencies (see line_pass_persistent). a.inst, a.n_inst and
+// the tick fields describe the whole tick; a.tw serves both passes (equal line lengths).
+template <int L>
+static cudaError_t launch_persist_tick(const LinePassArgs<float>& a, cudaStream_t st) {
+  using PG = PGeo<float, L>;
+  if constexpr (PG::CS != 1) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (!a.err || !a.inst || !a.n_inst || !a.tick_queue || !a.tick_done || a.tick_k < 1 ||
+        a.tick_k > PG::TICK_K_MAX ||
+        a.n_lines != L || a.n_lines % PG::GL != 0 || a.beta_im)
+      return cudaErrorInvalidValue;
+    auto kern = line_pass_persistent<float, L, true, true>;
+    static int max_blocks[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!max_blocks[dev]) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG::SMEM);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PG::THREADS, PG::SMEM);
+      if (e != cudaSuccess) return e;
+      if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+      max_blocks[dev] = per_sm * sm_count();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(max_blocks[dev], 1, 1);
+    cfg.blockDim = dim3(PG::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = PG::SMEM;
+    cfg.stream = st;
+    return cudaLaunchKernelEx(&cfg, kern, a, 0, a.err);
+  }
+}
+
+template <typename T>
+cudaError_t launch_line_pass_tick(const LinePassArgs<T>& a, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    switch (a.L) {
+      case 256: return launch_persist_tick<256>(a, st);
+      case 512: return launch_persist_tick<512>(a, st);
+      case 1024: return launch_persist_tick<1024>(a, st);
+      case 2048: return launch_persist_tick<2048>(a, st);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <typename T>
 int line_pass_radix(int L) { return radix_e<T>(L); }
+template <typename T>
+int line_pass_radix_alt(int L) { return radix_alt<T>(L); }
 
 }  // namespace dgb

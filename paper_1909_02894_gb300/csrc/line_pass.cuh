@@ -55,6 +55,7 @@ struct LinePassArgs {
   int n_lines;          // lines in the input = row length of the output
   int sigma;            // 0: sigma_x (x pass), 1: sigma_y (y pass)
   const Cx<T>* tw;      // per-pass twiddles, see tw_offset (at most L entries)
+  const Cx<T>* tw_alt;  // the same for the alternative radix schedule (or nullptr)
   const Q4<T>* mult;    // per k index q: step ((cos - 1) hi, lo, sin hi, lo) / (2L);
                         // derivative (0, 0, xi hi, xi lo) / L
   const T* beta;        // b - 1 per input point, or nullptr (b = 1)

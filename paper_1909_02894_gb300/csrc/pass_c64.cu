@@ -4,4 +4,6 @@
 namespace dgb {
 template cudaError_t launch_line_pass<float>(const LinePassArgs<float>&, int, int, cudaStream_t);
 template int line_pass_radix<float>(int);
+template int line_pass_radix_alt<float>(int);
+template cudaError_t launch_line_pass_tick<float>(const LinePassArgs<float>&, cudaStream_t);
 }  // namespace dgb

@@ -84,7 +84,12 @@ struct PGeo {
   // pass-3 twiddles of the digit-swap FFT: 8 warp slices x 8 entries (the 7 powers, a pad)
   static constexpr size_t OFF_T2 = OFF_T3 + 64 * sizeof(Cx<T>);
   // W_128^(u t) (t = 1..7 rows of 16) of the 1024-point FFT
-  static constexpr size_t SMEM = OFF_T2 + (SWAP1K ? 128 : 0) * sizeof(Cx<T>);
+  static constexpr size_t OFF_ITEM = OFF_T2 + (SWAP1K ? 128 : 0) * sizeof(Cx<T>);
+  // batched tick: a ring of three work items (5 ints each) and the item offsets of the
+  // tick's steps (at most TICK_K_MAX + 1)
+  static constexpr int TICK_K_MAX = 1024;
+  static constexpr size_t OFF_TPRE = OFF_ITEM + 16 * sizeof(int);
+  static constexpr size_t SMEM = OFF_TPRE + (TICK_K_MAX + 1) * sizeof(int);
   // tensor memory: 8 warps share each lane quarter; per warp slice s = warp / 4 the
   // parked spinor values take columns [16 s, 16 s + 16); the digit-swap FFT adds an
   // exchange region of 128 columns and 32 twiddle columns per slice
@@ -343,10 +348,26 @@ __device__ __forceinline__ void fft1024_swap(Cx<T> (&v)[8], Cx<T>* xw, int lane,
 // kernel parameter, which the compiler reads from the constant bank instead of keeping
 // in registers. Each instance has at most one of u_load / u_store (the U landing zone
 // holds one matrix field).
-template <typename T, int L, bool BATCH>
+// TICK (batched, square grids, no clusters): one launch runs every step of a batch tick.
+// Work items -- (step k, pass p, instance slot i, line group) in that order -- are taken
+// from a queue (*a0.tick_queue), two ahead of the one being worked on. Item (k, p, i) reads
+// what the previous pass of slot i wrote and overwrites what it read, so its rows are
+// requested only once all 2k + p earlier passes of slot i are finished:
+// a0.tick_done[i] >= (2k + p) line groups per pass. Thread 0 checks that when the item is
+// next (a counter value loaded early in the current iteration); if it is not yet true, the
+// item is marked and, at the start of its iteration, the CTA publishes its previous group
+// and thread 0 waits (a bounded spin, DIRAC_ETIMEOUT when it runs out). A finished group
+// is published one iteration late, after the next group's inverse FFT: every thread
+// fences its stores (long complete by then) before that CTA barrier, and thread 0 then
+// adds 1 to tick_done[i] with release semantics. An item only waits on earlier items, held
+// by running CTAs that publish before they wait, so every wait ends. A CTA that has failed
+// keeps taking items and counting them done (without work), so that no other CTA waits on
+// it.
+template <typename T, int L, bool BATCH, bool TICK = false>
 __global__ void __launch_bounds__(1024, 1)
     line_pass_persistent(const LinePassArgs<T> a0, int n_groups, int* __restrict__ err) {
   using PG = PGeo<T, L>;
+  static_assert(!TICK || (BATCH && PG::CS == 1), "ticks run batched, without clusters");
   using Gm = typename PG::G;
   constexpr int E = PG::E, J = L / E, LPI = PG::LPI, CS = PG::CS, GL = PG::GL;
   extern __shared__ __align__(128) unsigned char psmem[];
@@ -393,16 +414,18 @@ __global__ void __launch_bounds__(1024, 1)
       return a0;
     }
   };
-  auto issue_psi = [&](int grp) {  // thread 0
-    size_t first;
-    const LinePassArgs<T> x = args_of(grp, &first);
+  auto issue_psi_x = [&](const LinePassArgs<T>& x, size_t first) {  // thread 0
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bars[0], GROUP_BYTES + x.test_extra_tx);
     bulk_copy_g2s(psi_z, x.in + first, GROUP_BYTES, &bars[0]);
   };
-  auto issue_bu = [&](int grp) {  // thread 0; an empty request completes its phase at once
+  auto issue_psi = [&](int grp) {  // thread 0
     size_t first;
     const LinePassArgs<T> x = args_of(grp, &first);
+    issue_psi_x(x, first);
+  };
+  // thread 0; an empty request completes its phase at once
+  auto issue_bu_x = [&](const LinePassArgs<T>& x, size_t first) {
     const Q4<T>* usrc = x.u_load ? x.u_load : x.u_store;
     const uint32_t bytes =
         (x.beta ? (uint32_t)PG::BETA_BYTES : 0u) + (usrc ? (uint32_t)PG::U_BYTES : 0u);
@@ -418,6 +441,58 @@ __global__ void __launch_bounds__(1024, 1)
         bulk_copy_g2s(reinterpret_cast<unsigned char*>(u_z) + k * PG::U_PITCH,
                       usrc + first + k * (PG::U_CHUNK / sizeof(Q4<T>)), (uint32_t)PG::U_CHUNK,
                       &bars[1]);
+    }
+  };
+  auto issue_bu = [&](int grp) {
+    size_t first;
+    const LinePassArgs<T> x = args_of(grp, &first);
+    issue_bu_x(x, first);
+  };
+
+  // ---- batched tick: work item {k, p, i, gi, wait} (k < 0: none) broadcast through a
+  // shared-memory ring, slot it % 3 for iteration it; tpre[k] = first item of step k
+  int* s_item = reinterpret_cast<int*>(psmem + PG::OFF_ITEM);
+  int* tpre = reinterpret_cast<int*>(psmem + PG::OFF_TPRE);
+  auto tick_decode = [&](int t, int* out5) {  // thread 0: item number -> {k, p, i, gi, 0}
+    out5[4] = 0;
+    if (t >= tpre[a0.tick_k]) {
+      out5[0] = -1;
+      return;
+    }
+    int lo = 0, hi = a0.tick_k;  // tpre[lo] <= t < tpre[hi]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tpre[mid] <= t) lo = mid;
+      else hi = mid;
+    }
+    t -= tpre[lo];
+    const int per_pass = (tpre[lo + 1] - tpre[lo]) >> 1;
+    const int p = t >= per_pass ? 1 : 0;
+    t -= p * per_pass;
+    const int i = t / gpi;
+    out5[0] = lo;
+    out5[1] = p;
+    out5[2] = i;
+    out5[3] = t - i * gpi;
+  };
+  auto tick_args = [&](const int* it4, size_t* first) {
+    LinePassArgs<T> x = a0;
+    x.inst = a0.inst + ((size_t)it4[0] * 2 + it4[1]) * a0.inst_capacity;
+    bind_instance(x, it4[2]);
+    x.sigma = it4[1];
+    *first = (size_t)it4[3] * LPI * L;
+    return x;
+  };
+  auto tick_ready = [&](const int* it4) {  // thread 0
+    return ld_acquire_gpu(a0.tick_done + it4[2]) >= (2 * it4[0] + it4[1]) * gpi;
+  };
+  auto tick_wait = [&](const int* it4) {  // thread 0, bounded
+    const uint64_t t0 = global_ns();
+    while (!tick_ready(it4)) {
+      if (global_ns() - t0 > kWaitNs) {
+        atomicExch(err, kErrTimeout);
+        return;
+      }
     }
   };
 
@@ -440,6 +515,18 @@ __global__ void __launch_bounds__(1024, 1)
       const Cx<T>* w0 = a0.tw + tw_offset(512, 8);
       const Cx<T> w = ldg_cx(w0 + (e & 511));
       t2tab[tid] = e < 512 ? w : Cx<T>{-w.re, -w.im};
+    }
+  }
+  if constexpr (TICK) {
+    // item offsets of the steps, then the first two items
+    for (int k = tid; k < a0.tick_k; k += PG::THREADS) tpre[k + 1] = 2 * gpi * a0.n_inst[k];
+    __syncthreads();
+    if (tid == 0) {
+      tpre[0] = 0;
+      for (int k = 0; k < a0.tick_k; ++k) tpre[k + 1] += tpre[k];
+      tick_decode(atomicAdd(a0.tick_queue, 1), s_item);
+      tick_decode(atomicAdd(a0.tick_queue, 1), s_item + 5);
+      s_item[4] = 1;  // the first item's rows are requested at its iteration
     }
   }
   if (warp == 0) tmem_alloc(tslot, PG::TMEM_COLS);
@@ -484,9 +571,19 @@ __global__ void __launch_bounds__(1024, 1)
     tmem_st16(tlane + PG::T_TW + 16u * (uint32_t)slice, f);
     tmem_wait_st();
   }
-  if (tid == 0 && cluster_id < n_super) {
-    issue_psi(cluster_id * CS + rank);
-    issue_bu(cluster_id * CS + rank);
+  // TICK: the instance slot of the previous group, not yet published (-1: none)
+  int prev_i = -1;
+  if constexpr (TICK) {
+    if (tid == 0 && s_item[0] >= 0) {
+      size_t f;
+      const LinePassArgs<T> x = tick_args(s_item, &f);
+      issue_bu_x(x, f);
+    }
+  } else {
+    if (tid == 0 && cluster_id < n_super) {
+      issue_psi(cluster_id * CS + rank);
+      issue_bu(cluster_id * CS + rank);
+    }
   }
 
   // transposed store: this thread's line within an output segment (THREADS is a multiple
@@ -501,8 +598,9 @@ __global__ void __launch_bounds__(1024, 1)
   }
   bool failed = false;  // uniform across the CTA
   // copies requested / phases waited for, per mbarrier (uniform; at most one outstanding)
-  const uint32_t first_issue = cluster_id < n_super ? 1u : 0u;
-  uint32_t issued[2] = {first_issue, first_issue};
+  const uint32_t first_issue =
+      TICK ? (s_item[0] >= 0 ? 1u : 0u) : (cluster_id < n_super ? 1u : 0u);
+  uint32_t issued[2] = {TICK ? 0u : first_issue, first_issue};
   uint32_t done[2] = {0u, 0u};
   int it = 0;
   // clusters: the barrier after the transposed store is split; its arrive ends an
@@ -510,12 +608,55 @@ __global__ void __launch_bounds__(1024, 1)
   // forward FFT's shared-memory exchange), so the load and the first FFT passes overlap
   // the peer's gather. pend: an arrive awaits its wait (uniform across the cluster)
   bool pend = false;
-  for (int s = cluster_id; s < n_super; s += n_clusters, ++it) {
+  for (int s = cluster_id;; s += n_clusters, ++it) {
+    // TICK: this iteration's item, the next one and the one after (thread 0 decodes it)
+    int* cur = s_item + 5 * (it % 3);
+    int* nxt = s_item + 5 * ((it + 1) % 3);
+    int* nx2 = s_item + 5 * ((it + 2) % 3);
+    if constexpr (TICK) {
+      if (cur[0] < 0) break;
+    } else {
+      if (s >= n_super) break;
+    }
     const uint32_t par = (uint32_t)it & 1u;
     const int g = s * CS + rank;
     const bool has_next = s + n_clusters < n_super;
     size_t gfirst;
-    const LinePassArgs<T> a = args_of(g, &gfirst);
+    LinePassArgs<T> a;
+    if constexpr (TICK) a = tick_args(cur, &gfirst);
+    else a = args_of(g, &gfirst);
+    int ticket = 0;     // TICK, thread 0: the queue position two items ahead
+    int next_done = 0;  // TICK, thread 0: the next item's dependency counter, loaded early
+    if constexpr (TICK) {
+      if (failed) {  // no work: count the items done and keep taking them
+        if (tid == 0) {
+          if (prev_i >= 0) red_release_gpu_add(a0.tick_done + prev_i, 1);
+          red_release_gpu_add(a0.tick_done + cur[2], 1);
+          tick_decode(atomicAdd(a0.tick_queue, 1), nx2);
+        }
+        prev_i = -1;
+        __syncthreads();
+        continue;
+      }
+      if (cur[4]) {
+        // the rows were not ready when this item became next: publish the previous group
+        // (this item may depend on it), then wait for the item's dependencies
+        if (prev_i >= 0) __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+          if (prev_i >= 0) red_release_gpu_add(a0.tick_done + prev_i, 1);
+          tick_wait(cur);
+          fence_proxy_async_global();  // the previous pass's stores before the bulk copy
+          issue_psi_x(a, gfirst);
+          issued[0] += 1;
+        }
+        prev_i = -1;
+      }
+      if (tid == 0) {
+        ticket = atomicAdd(a0.tick_queue, 1);
+        if (nxt[0] >= 0) next_done = ld_acquire_gpu(a0.tick_done + nxt[2]);
+      }
+    }
     Cx<T> v[E];
     const int lrow = lcta * L;  // this line's first point within the group
     if (!failed) {
@@ -567,16 +708,33 @@ __global__ void __launch_bounds__(1024, 1)
         }
         tmem_st16(tpark, park);
       }
-      // The spinor zone has been read: every warp reports it on mbarrier 3, and thread 0
-      // requests the next group's rows once all have (no CTA-wide barrier here). A wait
-      // that ran out is folded into the CTA-wide check after the inverse FFT; until then
-      // the FFT runs on whatever the zone held.
-      if (__syncthreads_or(!ok)) {
+      // the spinor zone has been read: request the next group's rows
+      const bool bad = __syncthreads_or(!ok);
+      if constexpr (TICK) {
+        if (tid == 0) tick_decode(ticket, nx2);
+      }
+      if (bad) {
         failed = true;
         if (tid == 0) atomicExch(err, kErrTimeout);
+        if constexpr (TICK) {  // count the previous group done (the results are void)
+          if (tid == 0 && prev_i >= 0) red_release_gpu_add(a0.tick_done + prev_i, 1);
+          prev_i = -1;
+        }
       } else {
         done[0] += 1;
-        if (has_next) {
+        if constexpr (TICK) {
+          if (tid == 0 && nxt[0] >= 0) {
+            if (next_done >= (2 * nxt[0] + nxt[1]) * gpi) {
+              size_t f;
+              const LinePassArgs<T> x = tick_args(nxt, &f);
+              fence_proxy_async_global();  // the previous pass's stores before the copy
+              issue_psi_x(x, f);
+              issued[0] += 1;
+            } else {
+              nxt[4] = 1;  // requested at its iteration, after a wait
+            }
+          }
+        } else if (has_next) {
           if (tid == 0) issue_psi((s + n_clusters) * CS + rank);
           issued[0] += 1;
         }
@@ -636,9 +794,18 @@ __global__ void __launch_bounds__(1024, 1)
       else
         fft_passes<T, L, E, true>(v, buf2, j2, a.tw);
 
-      // b - 1 / U of this group; the barrier also frees the FFT buffer for staging
+      // b - 1 / U of this group; the barrier also frees the FFT buffer for staging (TICK:
+      // and publishes the previous group, whose stores completed long ago)
       const bool ok = mbar_wait_bounded(&bars[1], par, kWaitNs);
-      if (__syncthreads_or(!ok)) {
+      if constexpr (TICK) {
+        if (prev_i >= 0) __threadfence();
+      }
+      const bool bad_bu = __syncthreads_or(!ok);
+      if constexpr (TICK) {
+        if (tid == 0 && prev_i >= 0) red_release_gpu_add(a0.tick_done + prev_i, 1);
+        prev_i = -1;
+      }
+      if (bad_bu) {
         failed = true;
         if (tid == 0) atomicExch(err, kErrTimeout);
       } else {
@@ -712,7 +879,14 @@ __global__ void __launch_bounds__(1024, 1)
     // writes rows i of its L/CS slice, reading the owners' staging buffers. The barrier
     // publishes the staging writes and tells thread 0 that the b - 1 / U zone is free.
     if constexpr (CS > 1) cg::this_cluster().sync(); else __syncthreads();
-    if (!failed && has_next) {
+    if constexpr (TICK) {
+      if (!failed && tid == 0 && nxt[0] >= 0) {
+        size_t f;
+        const LinePassArgs<T> x = tick_args(nxt, &f);
+        issue_bu_x(x, f);
+        issued[1] += 1;
+      }
+    } else if (!failed && has_next) {
       if (tid == 0) issue_bu((s + n_clusters) * CS + rank);
       issued[1] += 1;
     }
@@ -770,6 +944,15 @@ __global__ void __launch_bounds__(1024, 1)
       pend = true;
     } else {
       __syncthreads();
+      // TICK: this group is published in the next iteration (or after the loop)
+      if constexpr (TICK) prev_i = cur[2];
+    }
+  }
+  if constexpr (TICK) {
+    if (prev_i >= 0) {
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) red_release_gpu_add(a0.tick_done + prev_i, 1);
     }
   }
   if constexpr (CS > 1) {

@@ -87,7 +87,9 @@ def test_autotuned_batch_equals_alone_runs_with_its_shapes(prec):
         D.dirac_batch_autotune(batch, 3)
         shapes = {n: D.dirac_batch_launch_shape(batch, n, n) for n in set(sizes)}
         for n, (tx, ty) in shapes.items():
-            assert tx in (256, 512, 1024) and ty in (256, 512, 1024), (n, tx, ty)
+            shapes_ok = (256, 512, 1024, 256 | D.DIRAC_LAUNCH_ALT_RADIX,
+                         512 | D.DIRAC_LAUNCH_ALT_RADIX)
+            assert tx in shapes_ok and ty in shapes_ok, (n, tx, ty)
             if prec == D.DIRAC_C128:
                 assert tx != 1024 and ty != 1024
         with pytest.raises(D.DiracError):

@@ -268,12 +268,17 @@ def test_norm_conserved_in_flat_space_on_gpu():
     assert abs(n1 / n0 - 1.0) <= 1e-12
 
 
+ALT = D.DIRAC_LAUNCH_ALT_RADIX
+SHAPES = [256, 512, 1024, 256 | ALT, 512 | ALT]
+
+
 @pytest.mark.parametrize("prec", PREC, ids=PID)
-@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("threads", SHAPES, ids=["256", "512", "1024", "256alt", "512alt"])
 @pytest.mark.parametrize("nx,ny", [(512, 256), (1024, 2048), (4096, 256), (256, 4096)])
 def test_every_cta_shape_matches_oracle(prec, threads, nx, ny):
     """All launch shapes, including the persistent prefetching pass (1024; complex64,
-    lines of 256..4096 points), give the oracle's result."""
+    lines of 256..4096 points) and the alternative radix schedules (radix-16 passes for
+    complex64, radix-8 for complex128), give the oracle's result."""
     ax, ay = 0.1 * nx, 0.1 * ny
     X, Y = W.mesh(nx, ny, ax, ay)
     g = 1.0 + 0.15 * np.exp(-((X - 0.2 * ax) ** 2 + Y ** 2) / (0.1 * ax * ay))
@@ -299,7 +304,7 @@ def test_autotune_keeps_state_and_picks_a_valid_shape(prec, tmp_path):
     with D.Simulation(w, precision=prec) as s:
         s.set_state(w.psi0)
         tx, ty = autotune.tune(s, prec, cache_path=str(tmp_path / "cache.json"), reps=5)
-        assert tx in (256, 512, 1024) and ty in (256, 512, 1024)
+        assert tx in SHAPES and ty in SHAPES
         s.step(6, w.dt)
         assert_parity(s.get_state(), ref, w, TOL[prec])
         assert autotune.tune(s, prec, cache_path=str(tmp_path / "cache.json")) == (tx, ty)
