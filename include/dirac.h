@@ -247,14 +247,15 @@ size_t dirac_footprint_bytes(const dirac_grid *grid, dirac_precision precision);
 
 /* ---- Batched stepping of many independent contexts (any mix of grid sizes).
  * Contexts of the same grid size form a class; one tick advances every active context
- * by up to steps_per_tick steps. A class of square complex64 grids with 256..2048-point
- * lines whose passes run the persistent pass (the default) takes its whole tick in ONE
- * persistent launch: work items (step, pass, context, line group) come from a queue, and
- * each waits -- bounded, DIRAC_ETIMEOUT when the bound runs out -- until the context's
- * previous pass is finished. Other classes launch, per step, one x-pass and one y-pass
- * over all their active contexts (also when the environment variable DIRAC_BATCH_TICK=0 is
- * set at dirac_batch_create). The classes run on parallel branches of a CUDA graph
- * captured once per class layout and replayed. Each context computes
+ * by up to steps_per_tick steps: per step and class, one x-pass and one y-pass launch
+ * over all of that class's active contexts. With the environment variable
+ * DIRAC_BATCH_TICK=1 set at dirac_batch_create, a class of square complex64 grids with
+ * 256..2048-point lines whose passes run the persistent pass takes its whole tick in ONE
+ * persistent launch instead: work items (step, pass, context, line group) come from a
+ * queue, and each waits -- bounded, DIRAC_ETIMEOUT when the bound runs out -- until the
+ * context's previous pass is finished (the same results; 4-8% slower per class on the
+ * 256-instance mix, hence not the default). The classes run on parallel branches of a
+ * CUDA graph captured once per class layout and replayed. Each context computes
  * exactly what dirac_step(ctx, n_steps, dt) computes (Sec. 5.2 Scheme II); a submitted
  * context belongs to the batch until it is released and must not be stepped, read or
  * destroyed meanwhile. Contexts must have the batch's precision. */

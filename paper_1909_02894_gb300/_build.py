@@ -10,8 +10,11 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(HERE, "libdirac.so")
+# DIRAC_BUILD_TAG=<tag> builds libdirac_<tag>.so (objects in _build_<tag>) beside the
+# default library, e.g. a debug build with DIRAC_NVCC_EXTRA="-DDIRAC_DEBUG=1".
+_TAG = os.environ.get("DIRAC_BUILD_TAG", "")
+BUILD = os.path.join(HERE, "_build" + (f"_{_TAG}" if _TAG else ""))
+LIB = os.path.join(HERE, "libdirac" + (f"_{_TAG}" if _TAG else "") + ".so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -3,7 +3,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Debug builds (nvcc -DDIRAC_DEBUG=1, see DIRAC_NVCC_EXTRA) check the index of each
+// memory access of the line passes against its buffer: a failed check sets this
+// translation unit's flag and the access is skipped (a load gives zero). Release builds
+// compile the checks away.
+#ifndef DIRAC_DEBUG
+#define DIRAC_DEBUG 0
+#endif
+
 namespace dgb {
+
+#if DIRAC_DEBUG
+static __device__ int g_dbg_bounds = 0;
+#endif
+// true when idx < bound (always, in release builds)
+__device__ __forceinline__ bool dbg_in(size_t idx, size_t bound) {
+#if DIRAC_DEBUG
+  if (idx >= bound) {
+    atomicExch(&g_dbg_bounds, 1);
+    return false;
+  }
+#endif
+  return true;
+}
 
 // Complex number in registers / shared memory.
 template <typename T>

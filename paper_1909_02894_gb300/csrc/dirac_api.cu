@@ -101,6 +101,8 @@ static dirac_status device_error(dirac_ctx* ctx) {
   int flag = 0;
   cudaError_t e = cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "read device error flag");
+  if (DIRAC_DEBUG && dgb_debug_bounds())
+    return fail(ctx, DIRAC_ECUDA, "debug build: an index check of a line pass failed");
   if (flag) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
     return fail(ctx, DIRAC_ETIMEOUT, "a bounded device wait ran out; the state is not valid");

@@ -30,6 +30,11 @@ int line_pass_radix(int L);
 // launch options 3 and 4 run it, with a twiddle table of that radix in tw_alt.
 template <typename T>
 int line_pass_radix_alt(int L);
+// Debug builds (-DDIRAC_DEBUG=1): read and clear the index-check flags of the line-pass
+// translation units; nonzero when a check failed. Always 0 in release builds.
+int dgb_debug_flag_c64();
+int dgb_debug_flag_c128();
+inline int dgb_debug_bounds() { return dgb_debug_flag_c64() | dgb_debug_flag_c128(); }
 
 // ---- FP64 precompute (precompute.cu)
 // a1, a2, meff, w and the two log fields (packed as a complex128 spinor (f1, f2)) from the

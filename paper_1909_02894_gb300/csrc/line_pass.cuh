@@ -347,7 +347,7 @@ __device__ __forceinline__ void pass_store(const Cx<T> (&v)[E], Cx<T>* buf, int 
       // NS = 1 only in the first pass (radix E, base a multiple of E + 1 slots); there the
       // t-th output is the next slot. NS a multiple of E adds NS + NS/E slots per step.
       const int o = (NS == 1) ? base + t : base + t * (NS + NS / E);
-      buf[o] = v[u + t * NB];
+      if (dbg_in(o, L + L / E)) buf[o] = v[u + t * NB];
     }
   }
 }
@@ -358,10 +358,16 @@ __device__ __forceinline__ void pass_load(Cx<T> (&v)[E], const Cx<T>* buf, int j
   if constexpr (J % E == 0) {
     const int b = spad<E>(j);
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[b + m * (J + J / E)];
+    for (int m = 0; m < E; ++m) {
+      const int o = b + m * (J + J / E);
+      v[m] = dbg_in(o, L + L / E) ? buf[o] : Cx<T>{T(0), T(0)};
+    }
   } else {
 #pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = buf[spad<E>(j + m * J)];
+    for (int m = 0; m < E; ++m) {
+      const int o = spad<E>(j + m * J);
+      v[m] = dbg_in(o, L + L / E) ? buf[o] : Cx<T>{T(0), T(0)};
+    }
   }
 }
 
@@ -444,7 +450,7 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
   for (int m = 0; m < E; ++m) {
     if ((m & 3) == 0) asm volatile("" ::: "memory");
     const size_t gi = row + j + m * J;
-    Cx<T> own = in_c[2 * gi];
+    Cx<T> own = dbg_in(gi, (size_t)a.n_lines * L) ? in_c[2 * gi] : Cx<T>{T(0), T(0)};
     if constexpr (MODE == MODE_STEP) {
       Cx<T> oth = shfl_pair(own);
       if (a.u_load) {
@@ -514,21 +520,27 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       Cx<T> d;
       if (c == 0) d = cadd_p(dp, dm);
       else d = a.sigma == 0 ? csub_p(dp, dm) : mul_i(csub_p(dp, dm));
-      Cx<T> p = in_c[2 * gi];
-      if (a.u_load) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
-      const T bm1 = a.beta ? a.beta[gi] : T(0);
+      const bool gi_ok = dbg_in(gi, (size_t)a.n_lines * L);
+      Cx<T> p = gi_ok ? in_c[2 * gi] : Cx<T>{T(0), T(0)};
+      if (a.u_load && gi_ok) p = apply_u_row(ldg_q4(a.u_load + gi), p, shfl_pair(p), c);
+      const T bm1 = (a.beta && gi_ok) ? a.beta[gi] : T(0);
       // (p + d) + (b - 1) d
       Cx<T> o = cfma_p(bm1, d, cadd_p(p, d));
       if (a.beta_im) {  // complex b - 1: add i Im(b - 1) d
-        const T bi = a.beta_im[gi];
+        const T bi = gi_ok ? a.beta_im[gi] : T(0);
         o = {o.re - bi * d.im, o.im + bi * d.re};
       }
-      if (a.u_store) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
-      if (a.store_normal) reinterpret_cast<Cx<T>*>(a.out)[2 * gi + c] = o;
-      else my_stage[2 * i] = o;
+      if (a.u_store && gi_ok) o = apply_u_row(ldg_q4(a.u_store + gi), o, shfl_pair(o), c);
+      if (a.store_normal) {
+        if (gi_ok) reinterpret_cast<Cx<T>*>(a.out)[2 * gi + c] = o;
+      }
+      else if (dbg_in(i, L + 1)) my_stage[2 * i] = o;
     } else {
-      if (a.store_normal) reinterpret_cast<Cx<T>*>(a.out)[2 * (row + i) + c] = v[m];
-      else my_stage[2 * i] = v[m];
+      if (a.store_normal) {
+        if (dbg_in(row + i, (size_t)a.n_lines * L))
+          reinterpret_cast<Cx<T>*>(a.out)[2 * (row + i) + c] = v[m];
+      }
+      else if (dbg_in(i, L + 1)) my_stage[2 * i] = v[m];
     }
   }
 
@@ -561,14 +573,16 @@ __global__ void __launch_bounds__(Geo<T, L, LPC, E>::THREADS,
       if constexpr (CS > 1) {
         if (owner != rank) src = cg::this_cluster().map_shared_rank(stage, owner);
       }
-      val[q] = src[(size_t)(g - owner * LPC) * (L + 1) + i];
+      const size_t si = (size_t)(g - owner * LPC) * (L + 1) + i;
+      val[q] = dbg_in(si, (size_t)LPC * (L + 1)) ? src[si] : Q4<T>{T(0), T(0), T(0), T(0)};
     }
 #pragma unroll
     for (int q = 0; q < HALF; ++q) {
       const int it = tid + (h * HALF + q) * Gm::THREADS;
       const int g = it % GL;
       const int i = i0 + it / GL;
-      a.out[(size_t)i * a.n_lines + line0 + g] = val[q];
+      if (dbg_in((size_t)i * a.n_lines + line0 + g, (size_t)a.n_lines * L))
+        a.out[(size_t)i * a.n_lines + line0 + g] = val[q];
     }
   }
   }

@@ -114,6 +114,11 @@ struct PGeo {
   }
   static __device__ __forceinline__ int upos_jm(int j, int m) { return spos_jm(j, m); }
   static_assert(!SWAP || L / E == PAD_EVERY, "padding every L/E points");
+  // entries of the landing zones and of the staging buffer (debug index checks)
+  static constexpr size_t PSI_N = (size_t)LPI * L;
+  static constexpr size_t BETA_N = CHUNKS * BETA_PITCH / sizeof(T);
+  static constexpr size_t U_N = CHUNKS * U_PITCH / sizeof(Q4<T>);
+  static constexpr size_t STAGE_N = SWAP ? STAGE_POINTS : (size_t)LPI * SPITCH;
 };
 
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
@@ -221,10 +226,16 @@ __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, i
   // passed) or the forward FFT (the barrier between the transforms).
   if (wait_cluster) cluster_wait();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) fc[(r & 1 ? wb1 : wb0) + 64 * r] = v[r];
+  for (int r = 0; r < 8; ++r) {
+    const int o = (r & 1 ? wb1 : wb0) + 64 * r;
+    if (dbg_in(o, 4096)) fc[o] = v[r];
+  }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = fc[(r & 1 ? rb1 : rb0) + 8 * r];
+  for (int r = 0; r < 8; ++r) {
+    const int o = (r & 1 ? rb1 : rb0) + 8 * r;
+    v[r] = dbg_in(o, 4096) ? fc[o] : Cx<T>{T(0), T(0)};
+  }
   dft8<T, INV>(v);
   {
     float f[16];
@@ -288,10 +299,12 @@ __device__ __forceinline__ void warp_xchg(Cx<T> (&v)[8], Cx<T>* xw, int lane) {
   Cx<T>* g = xw + ((lane & 1) + 2 * ((lane >> 1) & 1)) * XQ;
   const int l3 = lane >> 2;
 #pragma unroll
-  for (int r = 0; r < 8; ++r) g[l3 * XP + r] = v[r];
+  for (int r = 0; r < 8; ++r)
+    if (dbg_in(l3 * XP + r, XQ)) g[l3 * XP + r] = v[r];
   __syncwarp();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) v[r] = g[r * XP + l3];
+  for (int r = 0; r < 8; ++r)
+    v[r] = dbg_in(r * XP + l3, XQ) ? g[r * XP + l3] : Cx<T>{T(0), T(0)};
 }
 
 template <typename T, bool INV, int XP, int XQ>
@@ -415,6 +428,7 @@ __global__ void __launch_bounds__(1024, 1)
     }
   };
   auto issue_psi_x = [&](const LinePassArgs<T>& x, size_t first) {  // thread 0
+    if (!dbg_in(first + PG::PSI_N - 1, (size_t)x.n_lines * L)) first = 0;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&bars[0], GROUP_BYTES + x.test_extra_tx);
     bulk_copy_g2s(psi_z, x.in + first, GROUP_BYTES, &bars[0]);
@@ -426,6 +440,7 @@ __global__ void __launch_bounds__(1024, 1)
   };
   // thread 0; an empty request completes its phase at once
   auto issue_bu_x = [&](const LinePassArgs<T>& x, size_t first) {
+    if (!dbg_in(first + PG::PSI_N - 1, (size_t)x.n_lines * L)) first = 0;
     const Q4<T>* usrc = x.u_load ? x.u_load : x.u_store;
     const uint32_t bytes =
         (x.beta ? (uint32_t)PG::BETA_BYTES : 0u) + (usrc ? (uint32_t)PG::U_BYTES : 0u);
@@ -675,8 +690,9 @@ __global__ void __launch_bounds__(1024, 1)
           for (int h = 0; h < 2; ++h) {
             const int m = mm + h * (E / 2);
             const int i = j + m * J;
-            Q4<T> p = psi_z[i];
-            if (a.u_load) p = apply_u(u_z[PG::upos_jm(j, m)], p);
+            Q4<T> p = dbg_in(i, PG::PSI_N) ? psi_z[i] : Q4<T>{T(0), T(0), T(0), T(0)};
+            if (a.u_load && dbg_in(PG::upos_jm(j, m), PG::U_N))
+              p = apply_u(u_z[PG::upos_jm(j, m)], p);
             pp[h] = p;
             if (a.sigma == 0) v[m] = cfma_p(sg, Cx<T>{p.z, p.w}, Cx<T>{p.x, p.y});
             else v[m] = {p.x + sg * p.w, p.y - sg * p.z};
@@ -694,9 +710,9 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
         for (int m = 0; m < E; ++m) {
           const int i = j + m * J;
-          Cx<T> own = src_c[2 * i];
+          Cx<T> own = dbg_in(lrow + i, PG::PSI_N) ? src_c[2 * i] : Cx<T>{T(0), T(0)};
           Cx<T> oth = shfl_pair(own);
-          if (a.u_load) {
+          if (a.u_load && dbg_in(lrow + i, PG::U_N)) {
             own = apply_u_row(u_z[lrow + i], own, oth, c);
             oth = shfl_pair(own);
           }
@@ -817,7 +833,8 @@ __global__ void __launch_bounds__(1024, 1)
           // the neighbouring lane); thread c then finishes points m = 4c .. 4c + 3
           Cx<T>* stc = reinterpret_cast<Cx<T>*>(stage) + c;
 #pragma unroll
-          for (int m = 0; m < E; ++m) stc[2 * PG::spos_jm(j, m)] = v[m];
+          for (int m = 0; m < E; ++m)
+            if (dbg_in(PG::spos_jm(j, m), PG::STAGE_N)) stc[2 * PG::spos_jm(j, m)] = v[m];
           __syncwarp();
           float pk[2 * E];
           tmem_ld16(tpark, pk);
@@ -825,11 +842,14 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
           for (int mm = 0; mm < E / 2; ++mm) {
             const int m4 = 4 * c + mm;  // point j + m4 J
-            const Q4<T> dd = stage[PG::spos_jm(j, m4)];  // (D+, D-)
+            const bool sp_ok = dbg_in(PG::spos_jm(j, m4), PG::STAGE_N);
+            const Q4<T> dd = sp_ok ? stage[PG::spos_jm(j, m4)]  // (D+, D-)
+                                   : Q4<T>{T(0), T(0), T(0), T(0)};
             const Cx<T> dp = {dd.x, dd.y}, dm = {dd.z, dd.w};
             const Cx<T> d1 = cadd_p(dp, dm);
             const Cx<T> dd2 = csub_p(dp, dm);
-            const T bm1 = a.beta ? beta_z[PG::bpos_jm(j, m4)] : T(0);
+            const T bm1 = (a.beta && dbg_in(PG::bpos_jm(j, m4), PG::BETA_N))
+                              ? beta_z[PG::bpos_jm(j, m4)] : T(0);
             // psi + D + (b - 1) D per component
             const Cx<T> o1 = cfma_p(bm1, d1, cadd_p(Cx<T>{pk[4 * mm], pk[4 * mm + 1]}, d1));
             Cx<T> o2;
@@ -840,8 +860,9 @@ __global__ void __launch_bounds__(1024, 1)
               o2 = {(pk[4 * mm + 2] + d2.re) + bm1 * d2.re, (pk[4 * mm + 3] + d2.im) + bm1 * d2.im};
             }
             Q4<T> o = {o1.re, o1.im, o2.re, o2.im};
-            if (a.u_store) o = apply_u(u_z[PG::upos_jm(j, m4)], o);
-            stage[PG::spos_jm(j, m4)] = o;
+            if (a.u_store && dbg_in(PG::upos_jm(j, m4), PG::U_N))
+              o = apply_u(u_z[PG::upos_jm(j, m4)], o);
+            if (sp_ok) stage[PG::spos_jm(j, m4)] = o;
           }
         } else {
           Cx<T>* my_stage = reinterpret_cast<Cx<T>*>(stage + (size_t)lcta * PG::SPITCH) + c;
@@ -860,10 +881,11 @@ __global__ void __launch_bounds__(1024, 1)
               if (c == 0) d = cadd_p(dp, dm);
               else d = a.sigma == 0 ? csub_p(dp, dm) : mul_i(csub_p(dp, dm));
               const Cx<T> p = {pk[2 * mm], pk[2 * mm + 1]};
-              const T bm1 = a.beta ? beta_z[lrow + i] : T(0);
+              const T bm1 = (a.beta && dbg_in(lrow + i, PG::BETA_N)) ? beta_z[lrow + i] : T(0);
               Cx<T> o = cfma_p(bm1, d, cadd_p(p, d));  // (p + d) + (b - 1) d
-              if (a.u_store) o = apply_u_row(u_z[lrow + i], o, shfl_pair(o), c);
-              my_stage[2 * i] = o;
+              if (a.u_store && dbg_in(lrow + i, PG::U_N))
+                o = apply_u_row(u_z[lrow + i], o, shfl_pair(o), c);
+              if (dbg_in((size_t)lcta * PG::SPITCH + i, PG::STAGE_N)) my_stage[2 * i] = o;
             }
           }
         }
@@ -897,12 +919,14 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
       for (int q = 0; q < NIT; ++q) {
         const int idx = tid + q * PG::THREADS;
+        const bool out_ok = dbg_in(gfirst + idx, (size_t)a.n_lines * L);
         if constexpr (PG::SWAP) {  // one line; the padding of idx is idx / PAD_EVERY
-          a.out[gfirst + idx] =
-              stage[tid + tid / PG::PAD_EVERY + q * (PG::THREADS + PG::THREADS / PG::PAD_EVERY)];
+          const size_t si = tid + tid / PG::PAD_EVERY + q * (PG::THREADS + PG::THREADS / PG::PAD_EVERY);
+          if (out_ok && dbg_in(si, PG::STAGE_N)) a.out[gfirst + idx] = stage[si];
         } else {
           const int l = idx / L, i = idx - l * L;
-          a.out[gfirst + idx] = stage[(size_t)l * PG::SPITCH + PG::spos(i)];
+          const size_t si = (size_t)l * PG::SPITCH + PG::spos(i);
+          if (out_ok && dbg_in(si, PG::STAGE_N)) a.out[gfirst + idx] = stage[si];
         }
       }
     } else if (!failed) {
@@ -923,18 +947,23 @@ __global__ void __launch_bounds__(1024, 1)
         // gather through distributed shared memory from the owner's staged line
 #pragma unroll
         for (int q = 0; q < NIT; ++q)
-          val[q] = ld_dsmem_q4<T>(gsrc + (uint32_t)((sp0 + q * SPQ) * sizeof(Q4<T>)));
+          val[q] = dbg_in(sp0 + q * SPQ, PG::STAGE_N)
+                       ? ld_dsmem_q4<T>(gsrc + (uint32_t)((sp0 + q * SPQ) * sizeof(Q4<T>)))
+                       : Q4<T>{T(0), T(0), T(0), T(0)};
       } else {
 #pragma unroll
         for (int q = 0; q < NIT; ++q)
-          val[q] = stage[(size_t)gline * PG::SPITCH + sp0 + q * SPQ];
+          val[q] = dbg_in((size_t)gline * PG::SPITCH + sp0 + q * SPQ, PG::STAGE_N)
+                       ? stage[(size_t)gline * PG::SPITCH + sp0 + q * SPQ]
+                       : Q4<T>{T(0), T(0), T(0), T(0)};
       }
       Q4<T>* dst = a.out + (size_t)r0 * a.n_lines + line0 + gline;
       const size_t dstep = (size_t)RPI * a.n_lines;
 #pragma unroll
       for (int q = 0; q < NIT; ++q)  // streaming stores: the next pass reads them once
-        __stcs(reinterpret_cast<float4*>(dst + q * dstep),
-               make_float4(val[q].x, val[q].y, val[q].z, val[q].w));
+        if (dbg_in(r0 + q * RPI, L) && dbg_in(line0 + gline, a.n_lines))
+          __stcs(reinterpret_cast<float4*>(dst + q * dstep),
+                 make_float4(val[q].x, val[q].y, val[q].z, val[q].w));
     }
     // the staging buffer is free for the next super-group once every CTA of the cluster
     // has read it (the loads have returned: the stores above consumed them), so the

@@ -33,8 +33,12 @@ def alone(w, prec):
         return s.get_state()
 
 
+@pytest.mark.parametrize("tick", ["0", "1"], ids=["per-step", "tick-launch"])
 @pytest.mark.parametrize("prec", [D.DIRAC_C64, D.DIRAC_C128], ids=["c64", "c128"])
-def test_alone_equals_in_mix(prec):
+def test_alone_equals_in_mix(prec, tick, monkeypatch):
+    """Per-step launches and (DIRAC_BATCH_TICK=1) one persistent launch per tick for the
+    complex64 classes of 256..1024 points: every result equals its alone run bit for bit."""
+    monkeypatch.setenv("DIRAC_BATCH_TICK", tick)
     sizes = [128, 256, 128, 512, 256, 128, 1024, 256, 128, 512]
     steps = [37, 64, 5, 50, 16, 33, 20, 47, 64, 1]
     ws = mix(7, sizes, steps)

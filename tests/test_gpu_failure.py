@@ -77,11 +77,13 @@ def _alone(w, steps):
         return s.get_state()
 
 
-def test_batched_wait_timeout_is_reported_and_the_batch_recovers():
+@pytest.mark.parametrize("tick", ["0", "1"], ids=["per-step", "tick-launch"])
+def test_batched_wait_timeout_is_reported_and_the_batch_recovers(tick, monkeypatch):
     """A context whose first batched x pass waits for bytes that never arrive: the wait
     runs out, dirac_batch_poll reports DIRAC_ETIMEOUT for every context then in the batch,
     and after release, new states and resubmission the batch gives the alone results bit
-    for bit."""
+    for bit -- with per-step launches and with one persistent launch per tick."""
+    monkeypatch.setenv("DIRAC_BATCH_TICK", tick)
     rng = np.random.default_rng(5)
     ws = [W.batched_instance(n, rng, steps=6) for n in (512, 256, 1024, 512)]
     sims = [D.Simulation(w, precision=D.DIRAC_C64) for w in ws]
