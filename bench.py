@@ -7,7 +7,8 @@ strain bumps, absorbing layer 128, dt=0.05), whose state and coefficient fields 
 larger than L2, so no flush is needed between timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--workload large-4096|large-2048|graphene-1024-c64|graphene-1024-c128|plain-128-c128]
+                    [--workload large-4096|large-2048|large-4096-c128|graphene-1024-c64|
+                                graphene-1024-c128|plain-128-c128|batch-mix|serve]
 
 Prints one JSON line. The path does not shard: with N > 1 each rank runs an
 independent replica and `value` sums the ranks ("replicas only", weak scaling).
@@ -55,6 +56,8 @@ def workload(name):
         return W.graphene_strained(n=1024), "c128", 176
     if name == "plain-128-c128":
         return W.plain_128(), "c128", 176
+    if name == "large-4096-c128":
+        return W.large_4096(), "c128", 176
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -261,7 +264,8 @@ def run_reference(args, wl_name):
               "large-2048": lambda n: W.large_4096(n=n, steps=1),
               "graphene-1024-c64": lambda n: W.graphene_strained(n=n, steps=1),
               "graphene-1024-c128": lambda n: W.graphene_strained(n=n, steps=1),
-              "plain-128-c128": lambda n: W.plain_128(n=n, steps=1)}[wl_name]
+              "plain-128-c128": lambda n: W.plain_128(n=n, steps=1),
+              "large-4096-c128": lambda n: W.large_4096(n=n, steps=1)}[wl_name]
     steps, warm = max(1, args.steps), max(0, args.warmup)
     budget_s = 120.0
     n = 256 if w_full.nx >= 256 else w_full.nx
