@@ -120,9 +120,9 @@ def batch_traffic(count, pts):
         return None
 
 
-def ncu_traffic(workload_name):
+def ncu_traffic(workload_name, precision):
     """DRAM bytes per launch of the line pass from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    taken on the current kernel source, the same grid and the same precision; else None."""
     p = os.path.join(ROOT, "profiles", "line_pass_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -131,7 +131,8 @@ def ncu_traffic(workload_name):
         if "=" in line and not line.startswith("#"):
             k, v = line.split("=", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_hash") != kernel_hash() or kv.get("workload") != workload_name:
+    if (kv.get("kernel_hash") != kernel_hash() or kv.get("workload") != workload_name
+            or kv.get("precision") != precision):
         return None
     try:
         return float(kv["dram_bytes_per_launch"])
@@ -320,18 +321,32 @@ def cpu_baseline(w, scheme="printed", degree=8, check_steps=0):
             return oracle.run(prob, wl.psi0, wl.dt, n, scheme=1 if scheme == "symmetric" else 0)
         return run
 
+    def timed(run, n):
+        t0 = time.perf_counter()
+        out = run(n)
+        return time.perf_counter() - t0, out
+
+    def per_step(run, k, tk, t1, min_diff=2.0, max_rounds=4):
+        """Seconds per step from the difference of a k-step and a 1-step run; on a grid so
+        small that the difference is under min_diff seconds (timer noise and the fixed
+        set-up of a run would dominate), longer runs until it is not."""
+        for _ in range(max_rounds):
+            if tk - t1 >= min_diff:
+                break
+            diff = tk - t1
+            k = int(k * min(64.0, max(2.0, 1.5 * min_diff / diff))) if diff > 0.01 else k * 64
+            tk, _ = timed(run, k)
+        return max(tk - t1, 1e-9) / (k - 1), k
+
     k = max(2, check_steps)
     run = runner(w)
-    t0 = time.perf_counter()
-    run(1)
-    t1 = time.perf_counter()
-    state = run(k)
-    t2 = time.perf_counter()
-    per_step = max(((t2 - t1) - (t1 - t0)) / (k - 1), 1e-9)
+    t1, _ = timed(run, 1)
+    tk, state = timed(run, k)
+    sec, m = per_step(run, k, tk, t1)
     cores = oracle.threads()
-    rec = {"value": w.nx * w.ny / per_step, "unit": UNIT, "cores": cores, "kind": "oracle",
-           "sample": f"difference of {k}-step and 1-step FP64 oracle runs on {w.name}, "
-                     f"divided by {k - 1}"}
+    rec = {"value": w.nx * w.ny / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"difference of {m}-step and 1-step FP64 oracle runs on {w.name}, "
+                     f"divided by {m - 1}"}
     # one core, on a smaller grid of the same recipe when the full grid is large
     small = w
     if w.nx * w.ny > 1024 * 1024 and w.name.startswith("large-"):
@@ -339,14 +354,12 @@ def cpu_baseline(w, scheme="printed", degree=8, check_steps=0):
     try:
         oracle.set_threads(1)
         run1 = runner(small)
-        t0 = time.perf_counter()
-        run1(1)
-        t1 = time.perf_counter()
-        run1(2)
-        t2 = time.perf_counter()
+        t1, _ = timed(run1, 1)
+        t2, _ = timed(run1, 2)
+        sec, m = per_step(run1, 2, t2, t1, min_diff=1.0)
         rec["single_thread"] = {
-            "value": small.nx * small.ny / max((t2 - t1) - (t1 - t0), 1e-9), "unit": UNIT,
-            "cores": 1, "sample": f"difference of 2-step and 1-step runs on {small.name}"}
+            "value": small.nx * small.ny / sec, "unit": UNIT, "cores": 1,
+            "sample": f"difference of {m}-step and 1-step runs on {small.name}, divided by {m - 1}"}
     finally:
         oracle.set_threads(cores)
     return rec, state
@@ -755,7 +768,7 @@ def main():
         bytes_pt = (iters * per_iter + args.steps * (3 * apply_b + 2 * s_ + 16)) / args.steps
         achieved = bytes_pt * pts / (ms * 1e-3 / args.steps) / 1e9
         krylov = {"arnoldi_steps_per_step": iters / args.steps}
-    traffic = None if (symmetric or poly or cn) else ncu_traffic(args.workload)
+    traffic = None if (symmetric or poly or cn) else ncu_traffic(w.name, prec_name)
 
     # ---- rel-L2 of the GPU result against the FP64 oracle (full grid, a few steps), and
     # the oracle's own rate on the host cores from the same runs

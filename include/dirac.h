@@ -205,10 +205,11 @@ long dirac_krylov_iterations(const dirac_ctx *ctx);
  * CTA; complex128: 1 to 4 lines per CTA, 32 to 512 threads), 1024 the persistent
  * prefetching variant (complex64, lines of 256..4096 points; one CTA per SM streams the
  * next lines into shared memory while it transforms the current ones); 0 = the default
- * (complex64: persistent for lines of 1024 points or more, the smaller shape for
- * 256-point lines, else the larger;
- * complex128: the smaller shape for 1024-point lines, else the larger). Lines of 128
- * points or fewer and 4096-point lines have one shape only. 256 or 512 plus
+ * (complex64: persistent for lines of 1024 points or more, the smaller shape for 128-
+ * and 256-point lines, else the larger; complex128: the smaller shape for 1024-point
+ * lines and lines of 128 points or fewer, else the larger). 64- and 128-point lines take
+ * 2 or 16 lines per CTA; lines of 32 points or fewer and 4096-point lines have one shape
+ * only. 256 or 512 plus
  * DIRAC_LAUNCH_ALT_RADIX selects the other radix schedule of the FFT passes, where the line
  * length has one: complex64 lines of 256..4096 points in radix-16 instead of radix-8
  * passes, complex128 lines of 256..2048 points in radix-8 instead of radix-16 passes, each

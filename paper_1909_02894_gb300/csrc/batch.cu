@@ -381,12 +381,12 @@ static dirac_status run_tick(dirac_batch* b, int K) {
 }
 
 // Shapes worth timing for a pass over lines of L points (the launcher maps the others onto
-// these): complex64 256..4096 points also the persistent pass; lines of 128 points or
+// these): complex64 256..4096 points also the persistent pass; lines of 32 points or
 // fewer and 4096-point lines have one non-persistent shape.
 template <typename T>
 static std::vector<int> shape_candidates(int L) {
   std::vector<int> o;
-  if (L > 128 && L < 4096) o.push_back(0);
+  if (L >= 64 && L < 4096) o.push_back(0);
   o.push_back(1);
   if (sizeof(T) == 4 && L >= 256) o.push_back(2);
   if (line_pass_radix_alt<T>(L)) {  // the other radix schedule (3 smaller, 4 larger CTA)

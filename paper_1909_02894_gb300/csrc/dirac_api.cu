@@ -88,12 +88,14 @@ static int pass_opt(const dirac_ctx* ctx, int shape, int L) {
   if (threads == 512) return 1;
   if (threads == 1024) return 2;
   // Default, by measurement on the strained-graphene grids: complex64 the persistent
-  // prefetching pass for lines of 1024 points or more, the smaller shape for 256-point
-  // lines (0.016 against 0.018 ms per 256^2 step), else the larger; complex128 the smaller
-  // shape for 1024-point lines (one line per CTA: 1024 CTAs spread over the SMs to within
-  // one line, 0.74 against 0.89 ms per 1024^2 step), else the larger.
-  if (ctx->prec == DIRAC_C64) return L >= 1024 ? 2 : L == 256 ? 0 : 1;
-  return L == 1024 ? 0 : 1;
+  // prefetching pass for lines of 1024 points or more, the smaller shape for 128- and
+  // 256-point lines (0.016 against 0.018 ms per 256^2 step, 0.0166 against 0.0187 per
+  // 128^2), else the larger; complex128 the smaller shape for 1024-point lines (one line
+  // per CTA: 1024 CTAs spread over the SMs to within one line, 0.74 against 0.89 ms per
+  // 1024^2 step) and for lines of 128 points or fewer (0.050 against 0.168 ms per 128^2
+  // step), else the larger.
+  if (ctx->prec == DIRAC_C64) return L >= 1024 ? 2 : (L == 256 || L == 128) ? 0 : 1;
+  return (L == 1024 || L <= 128) ? 0 : 1;
 }
 
 // Reads and clears the device error flag (after the stream has been synchronised).

@@ -9,9 +9,14 @@ namespace dgb {
 
 // Elements per thread: FP32 lines of 256 points or more use E = 8 (radix-8 passes; the
 // FFT state of a thread fits the 64-register budget of 1024 threads per SM without
-// spilling); shorter lines and FP64 use E = 16.
+// spilling), and so do 64- and 128-point lines in both precisions (twice the threads per
+// line: a small grid's pass is bound by the latency of each warp's dependent chain, and
+// halving the chain measured 0.086 -> 0.050 ms per 128^2 complex128 step); the other
+// lengths use E = 16.
 template <typename T>
-constexpr int radix_e(int L) { return (sizeof(T) == 4 && L >= 256) ? 8 : 16; }
+constexpr int radix_e(int L) {
+  return ((sizeof(T) == 4 && L >= 256) || L == 64 || L == 128) ? 8 : 16;
+}
 // The other radix schedule the autotuner may choose (0: none): FP32 lines of 256..4096
 // points in radix-16 passes, FP64 lines of 256..2048 points in radix-8 passes.
 template <typename T>
@@ -55,21 +60,34 @@ static cudaError_t launch_one(const LinePassArgs<T>& a, cudaStream_t st) {
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-// Two CTA shapes per line length (opt 0 smaller, opt 1 larger; lines of 128 points or
+// Two CTA shapes per line length (opt 0 smaller, opt 1 larger; lines of 32 points or
 // fewer and 4096-point lines have one). Lines per CTA, by precision:
 //   FP32 (E = 8 from 256 points): 256: 4|8, 512: 2|4, 1024: 1|2, 2048: 1|2, 4096: 1
 //     (256|512 threads, 512|1024 at 2048, 1024 at 4096)
-//   FP64 (E = 16): 256: 1|2, 512: 2|4, 1024: 1|2, 2048: 1|2, 4096: 1 (32..512 threads).
+//   FP64 (E = 16 from 256 points): 256: 1|2, 512: 2|4, 1024: 1|2, 2048: 1|2, 4096: 1 (32..512 threads).
 //     The FP64 pass is bound by the FP64 units and its CTAs hold 128-162 registers per
 //     thread, so few CTAs fit an SM: small CTAs keep all 152 SMs evenly loaded. Measured on
 //     the strained-graphene grids (ms per step, opt 0 | opt 1): 256^2 0.096 | 0.096,
 //     512^2 0.203 | 0.199, 1024^2 0.741 | 0.886, 2048^2 3.61 | 3.20; the shapes used before
 //     (256: 8|16, 512: 4|8, 1024: 2|4) took 0.180 | 0.350, 0.199 | 0.387, 0.885 | 0.832.
-//   both: 16 lines per CTA up to 128 points.
+//   both: 64 and 128 points (E = 8) 2|16 lines per CTA, 16 and 32 points 16. Measured
+//     (ms per step, opt 0 | opt 1): complex128 64^2 0.045 | 0.078, 128^2 0.050 | 0.168;
+//     complex64 64^2 0.0156 | 0.0146, 128^2 0.0166 | 0.0187.
 template <typename T, int MODE>
 static cudaError_t dispatch(const LinePassArgs<T>& a, int opt, cudaStream_t st) {
   constexpr bool F = sizeof(T) == 4;
   const bool big = (MODE == MODE_STEP) && opt != 0;
+  if constexpr (MODE == MODE_STEP) {
+    // 64- and 128-point lines: 2 lines per CTA as the smaller shape (one or two warps; a
+    // small grid then spreads over 8x as many CTAs), 16 as the larger
+    if (!big) {
+      switch (a.L) {
+        case 64: return launch_one<T, 64, 2, MODE>(a, st);
+        case 128: return launch_one<T, 128, 2, MODE>(a, st);
+        default: break;
+      }
+    }
+  }
   switch (a.L) {
     case 16: return launch_one<T, 16, 16, MODE>(a, st);
     case 32: return launch_one<T, 32, 16, MODE>(a, st);

@@ -56,3 +56,23 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = bench.argparse.Namespace(steps=3, warmup=3, gpus=2)
     assert bench.run_reference(args, "large-4096") == 0
     assert capsys.readouterr().out == ""
+
+
+def test_traffic_summaries_are_keyed_as_the_bench_looks_them_up(tmp_path, monkeypatch):
+    """The committed ncu traffic summaries are found under the names bench.py passes (the
+    workload's grid name and precision, the batch mix's size), and only there."""
+    from paper_1909_02894_gb300 import workloads as W
+
+    name = W.large_4096(n=64, steps=1).name.replace("64", "4096")
+    assert name == "large-4096^2"
+    h = bench.kernel_hash()
+    f = tmp_path / "profiles"
+    f.mkdir()
+    (f / "line_pass_traffic.txt").write_text(
+        f"# c\nworkload = {name}\nprecision = c64\nkernel_hash = {h}\n"
+        "dram_bytes_per_launch = 123\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_hash", lambda: h)
+    assert bench.ncu_traffic(name, "c64") == 123.0
+    assert bench.ncu_traffic(name, "c128") is None
+    assert bench.ncu_traffic("large-4096", "c64") is None

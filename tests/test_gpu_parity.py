@@ -274,7 +274,8 @@ SHAPES = [256, 512, 1024, 256 | ALT, 512 | ALT]
 
 @pytest.mark.parametrize("prec", PREC, ids=PID)
 @pytest.mark.parametrize("threads", SHAPES, ids=["256", "512", "1024", "256alt", "512alt"])
-@pytest.mark.parametrize("nx,ny", [(512, 256), (1024, 2048), (4096, 256), (256, 4096)])
+@pytest.mark.parametrize("nx,ny", [(512, 256), (1024, 2048), (4096, 256), (256, 4096),
+                                   (128, 64), (64, 128)])
 def test_every_cta_shape_matches_oracle(prec, threads, nx, ny):
     """All launch shapes, including the persistent prefetching pass (1024; complex64,
     lines of 256..4096 points) and the alternative radix schedules (radix-16 passes for
