@@ -154,7 +154,8 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 // Orders this thread's earlier generic-proxy shared-memory accesses before later
-// async-proxy (bulk copy) writes to the same memory.
+// async-proxy operations on the same memory (bulk copies that write it, bulk and tensor
+// stores that read it).
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -214,6 +215,34 @@ __device__ __forceinline__ void red_release_gpu_add(int* p, int v) {
 // async-proxy (bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// ---- asynchronous stores from shared memory (bulk-group completion)
+// Tiled tensor store of one 2D box from shared memory (128-B aligned) to global memory,
+// at element coordinates (x, y) of the tensor map; x times the element size a multiple of
+// 16 bytes, neither coordinate negative.
+__device__ __forceinline__ void tma_store_2d(const void* tmap, uint32_t smem, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(tmap),
+      "r"(smem), "r"(x), "r"(y)
+      : "memory");
+}
+// Bulk store of `bytes` (a multiple of 16) from shared to global memory, both 16-B aligned.
+__device__ __forceinline__ void bulk_copy_s2g(void* dst, uint32_t smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// every committed bulk store of this thread has read its shared-memory source
+__device__ __forceinline__ void bulk_wait_read_all() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// every committed bulk store of this thread is complete
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // Address of the same shared-memory variable in CTA `rank` of the cluster.

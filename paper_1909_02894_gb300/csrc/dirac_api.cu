@@ -107,6 +107,9 @@ static dirac_status device_error(dirac_ctx* ctx) {
     return fail(ctx, DIRAC_ECUDA, "debug build: an index check of a line pass failed");
   if (flag) {
     cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (flag == 2)  // the 4096-point pass's staging tile (never expected)
+      return fail(ctx, DIRAC_ECUDA, "a line pass found its shared-memory staging tile "
+                                    "misaligned for tensor stores; the state is not valid");
     return fail(ctx, DIRAC_ETIMEOUT, "a bounded device wait ran out; the state is not valid");
   }
   return DIRAC_OK;

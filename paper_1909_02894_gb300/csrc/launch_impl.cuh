@@ -1,6 +1,8 @@
 // Launch logic of the fused line pass, instantiated once per precision.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include "internal.h"
 #include "persist_pass.cuh"
@@ -124,6 +126,38 @@ static int sm_count() {
   return cached[dev];
 }
 
+// Tensor map of a transposed complex64 output out[rows][n_lines] (16-byte points) as a 2D
+// float tensor of 4 n_lines x rows, with boxes of 4 x 256 (one point of 256 rows): a
+// staged 4096-point line is 16 such boxes. The encoder is taken from the driver at the
+// first call.
+static cudaError_t out_tensor_map(CUtensorMap* m, void* out, int n_lines, int rows) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static const Encode encode = []() -> Encode {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<Encode>(fn);
+  }();
+  if (!encode) return cudaErrorNotSupported;
+  if (n_lines < 1 || rows % 256 != 0 || (reinterpret_cast<uintptr_t>(out) & 15))
+    return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)4 * (cuuint64_t)n_lines, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)n_lines * 16};  // bytes between rows
+  const cuuint32_t box[2] = {4, 256};
+  const cuuint32_t elem_strides[2] = {1, 1};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, out, dims, strides, box,
+                            elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Persistent prefetching variant (complex64 step mode, 256..4096-point lines): one
 // 1024-thread CTA per SM (clusters of 2 for 4096-point lines), as
 // many as can be resident, at most one per group of 4096 points.
@@ -165,7 +199,13 @@ static cudaError_t launch_persist(const LinePassArgs<float>& a, cudaStream_t st)
   int clusters = cached;
   if (clusters > groups / PG::CS) clusters = groups / PG::CS;
   cfg.gridDim = dim3(clusters * PG::CS, 1, 1);
-  return cudaLaunchKernelEx(&cfg, kern, a, groups, a.err);
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof(tmap));
+  if (L == 4096 && !a.inst && !a.store_normal) {  // the tensor stores of the output tiles
+    e = out_tensor_map(&tmap, a.out, a.n_lines, L);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, a, groups, a.err, tmap);
 }
 
 // The alternative radix schedule (radix_alt), opt 3 the smaller and opt 4 the larger of two
@@ -254,7 +294,9 @@ static cudaError_t launch_persist_tick(const LinePassArgs<float>& a, cudaStream_
     cfg.blockDim = dim3(PG::THREADS, 1, 1);
     cfg.dynamicSmemBytes = PG::SMEM;
     cfg.stream = st;
-    return cudaLaunchKernelEx(&cfg, kern, a, 0, a.err);
+    CUtensorMap tmap;
+    memset(&tmap, 0, sizeof(tmap));
+    return cudaLaunchKernelEx(&cfg, kern, a, 0, a.err, tmap);
   }
 }
 

@@ -14,16 +14,23 @@
 // So a group's critical path holds no global-memory load but the k-space multipliers and
 // twiddles (cached tables). The FFT, k-space multiply, inverse FFT and epilogue are those
 // of line_pass_kernel (eigencomponent per thread, radix-8 passes). The output leaves in
-// the transposed layout as segments of LPI lines; for 4096-point lines the CTAs run as
-// clusters of 2 that gather their staged lines through distributed shared memory into
-// 2-line segments. 4096- and 1024-point lines run FFTs whose exchanges go through tensor
-// memory (fft4096_swap, fft1024_swap); the other lengths run the Stockham passes.
+// the transposed layout as segments of LPI lines. 4096-point lines run as clusters of 2
+// CTAs (adjacent lines): in single-instance launches each CTA stages its finished line in
+// shared memory and thread 0 writes it with asynchronous tensor stores (one point per
+// row, 256 rows per box), which drain while the next group loads and transforms; the two
+// CTAs write the two 16-byte halves of each 32-byte sector at about the same time.
+// Batched launches gather the two staged lines through distributed shared memory into
+// 32-byte segments and store them from registers. 4096- and 1024-point lines run FFTs
+// whose exchanges go through tensor memory (fft4096_swap, fft1024_swap); the other
+// lengths run the Stockham passes.
 //
 // Every wait on an mbarrier is bounded: if one runs out, the CTA records an error code
 // in *err, stops issuing copies and transforming, keeps taking part in the cluster
 // barriers until its peers finish (so none of them waits forever), waits (bounded) for
 // the copies it issued itself, frees its tensor memory and returns.
 #pragma once
+#include <cuda.h>  // CUtensorMap
+
 #include "line_pass.cuh"
 
 namespace dgb {
@@ -123,6 +130,7 @@ struct PGeo {
 
 constexpr uint64_t kWaitNs = 1500000000ull;  // 1.5 s: a copy of 64 KB takes microseconds
 constexpr int kErrTimeout = 1;
+constexpr int kErrAlign = 2;  // the staging tile of the tensor stores is not 128-B aligned
 
 // ---- digit-swap FFT of 4096 points (forward, or inverse without the 1/N scale)
 //
@@ -190,11 +198,13 @@ __device__ __forceinline__ void tmem_swap(Cx<T> (&v)[8], uint32_t x, int s, int 
 // tws: this thread's pass-1 and pass-2 twiddles parked in tensor memory (w^1..w^7 of
 // each, 16 columns apart); x: the exchange region; fc: this component's 4096-point shared
 // buffer and cx its slot XOR (0 or 9, see swz4096); t3: the warp slice's pass-3 twiddles
-// W_64^(d0 t), t = 1..7, in shared memory (one broadcast read each).
+// W_64^(d0 t), t = 1..7, in shared memory (one broadcast read each). pre: what precedes
+// the first write of the shared buffer (0 nothing, 1 the wait of a split cluster barrier,
+// 2 thread 0 waits until its bulk stores have read the buffer, then a CTA barrier).
 template <typename T, bool INV>
 __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, int j, int s,
                                              int q, uint32_t tws, uint32_t x,
-                                             const Cx<T>* t3, bool wait_cluster = false) {
+                                             const Cx<T>* t3, int pre = 0) {
   {
     float t1[16];
     tmem_ld16(tws, t1);
@@ -222,9 +232,13 @@ __device__ __forceinline__ void fft4096_swap(Cx<T> (&v)[8], Cx<T>* fc, int cx, i
   const int m3 = (m >> 3) & 1;  // flips bit 3, the low bit of r's field
   const int rb0 = rbase + 8 * m3, rb1 = rbase - 8 * m3;
   // Earlier readers of the buffer have finished: the previous group's gather (the wait of
-  // the split cluster barrier, here when wait_cluster is set, or a barrier the caller
-  // passed) or the forward FFT (the barrier between the transforms).
-  if (wait_cluster) cluster_wait();
+  // the split cluster barrier, pre = 1, or a barrier the caller passed), its bulk stores
+  // (pre = 2) or the forward FFT (the barrier between the transforms).
+  if (pre == 1) cluster_wait();
+  if (pre == 2) {
+    if (threadIdx.x == 0) bulk_wait_read_all();
+    __syncthreads();
+  }
 #pragma unroll
   for (int r = 0; r < 8; ++r) {
     const int o = (r & 1 ? wb1 : wb0) + 64 * r;
@@ -376,13 +390,25 @@ __device__ __forceinline__ void fft1024_swap(Cx<T> (&v)[8], Cx<T>* xw, int lane,
 // by running CTAs that publish before they wait, so every wait ends. A CTA that has failed
 // keeps taking items and counting them done (without work), so that no other CTA waits on
 // it.
+// TST (single-instance 4096-point launches): each thread writes its finished points into
+// the CTA's staged line (point i at slot i, no padding); after a CTA barrier thread 0
+// writes it with 16 tensor stores (tmap_out: the output as a 2D float tensor of
+// 4 n_lines x L, boxes of 4 x 256, one 16-byte point per row), or, for rows back in the
+// input's layout, with one bulk store. Before the next group's first write into the shared
+// buffer thread 0 waits until its stores have read the staged line. No cluster barrier:
+// the CTAs of a cluster only run adjacent lines at the same time. Other launches take a
+// zero tmap_out.
 template <typename T, int L, bool BATCH, bool TICK = false>
 __global__ void __launch_bounds__(1024, 1)
-    line_pass_persistent(const LinePassArgs<T> a0, int n_groups, int* __restrict__ err) {
+    line_pass_persistent(const LinePassArgs<T> a0, int n_groups, int* __restrict__ err,
+                         const __grid_constant__ CUtensorMap tmap_out) {
   using PG = PGeo<T, L>;
   static_assert(!TICK || (BATCH && PG::CS == 1), "ticks run batched, without clusters");
   using Gm = typename PG::G;
   constexpr int E = PG::E, J = L / E, LPI = PG::LPI, CS = PG::CS, GL = PG::GL;
+  constexpr bool TST = PG::SWAP && CS > 1 && !BATCH;
+  constexpr int TBOX = 256;  // rows per tensor store
+  static_assert(!TST || (LPI == 1 && (size_t)L * sizeof(Q4<T>) <= PG::F_BYTES), "staged line");
   extern __shared__ __align__(128) unsigned char psmem[];
   Cx<T>* fbuf = reinterpret_cast<Cx<T>*>(psmem);
   Q4<T>* psi_z = reinterpret_cast<Q4<T>*>(psmem + PG::OFF_PSI);
@@ -612,6 +638,12 @@ __global__ void __launch_bounds__(1024, 1)
            (uint32_t)((gline - owner * LPI) * PG::SPITCH * sizeof(Q4<T>));
   }
   bool failed = false;  // uniform across the CTA
+  if constexpr (TST) {
+    if (smem_u32(psmem) & 127u) {  // tensor stores read 128-B aligned boxes
+      failed = true;
+      if (tid == 0) atomicExch(err, kErrAlign);
+    }
+  }
   // copies requested / phases waited for, per mbarrier (uniform; at most one outstanding)
   const uint32_t first_issue =
       TICK ? (s_item[0] >= 0 ? 1u : 0u) : (cluster_id < n_super ? 1u : 0u);
@@ -673,6 +705,7 @@ __global__ void __launch_bounds__(1024, 1)
       }
     }
     Cx<T> v[E];
+    Q4<T> o_out[TST ? E / 2 : 1];  // TST: this thread's finished points m = 4c .. 4c + 3
     const int lrow = lcta * L;  // this line's first point within the group
     if (!failed) {
       // a thread whose wait ran out reads whatever the zone holds; the barrier after the
@@ -764,7 +797,7 @@ __global__ void __launch_bounds__(1024, 1)
           if (pend) cluster_wait();
         fft4096_swap<T, false>(v, fbuf + c * L, 9 * c, j, slice, quarter,
                                tlane + PG::T_TW + 32u * (uint32_t)slice, tlane + PG::T_X,
-                               t3tab + 8 * slice, !BATCH && CS > 1 && pend);
+                               t3tab + 8 * slice, TST ? 2 : (!BATCH && CS > 1 && pend) ? 1 : 0);
         pend = false;
       } else if constexpr (PG::SWAP1K) {
         fft1024_swap<T, false, PG::XP, PG::XQ>(v, xw, lane, slice, quarter,
@@ -828,7 +861,38 @@ __global__ void __launch_bounds__(1024, 1)
         done[1] += 1;
         tmem_wait_st();
         Q4<T>* stage = reinterpret_cast<Q4<T>*>(psmem);
-        if constexpr (PG::SWAP) {
+        if constexpr (TST) {
+          // the pair's eigencomponents meet through a shuffle (the shared buffer holds the
+          // staged line here); thread c finishes points m = 4c .. 4c + 3
+          float pk[2 * E];
+          tmem_ld16(tpark, pk);
+          tmem_wait_ld_regs(pk);
+#pragma unroll
+          for (int mm = 0; mm < E / 2; ++mm) {
+            const int m4 = 4 * c + mm;
+            const Cx<T> snd = c ? v[mm] : v[mm + E / 2];  // the partner's points
+            const Cx<T> mine = c ? v[mm + E / 2] : v[mm];
+            const Cx<T> rcv = {__shfl_xor_sync(0xffffffffu, snd.re, 1),
+                               __shfl_xor_sync(0xffffffffu, snd.im, 1)};
+            const Cx<T> dp = c ? rcv : mine, dm = c ? mine : rcv;  // (D+, D-)
+            const Cx<T> d1 = cadd_p(dp, dm);
+            const Cx<T> dd2 = csub_p(dp, dm);
+            const T bm1 = (a.beta && dbg_in(PG::bpos_jm(j, m4), PG::BETA_N))
+                              ? beta_z[PG::bpos_jm(j, m4)] : T(0);
+            const Cx<T> o1 = cfma_p(bm1, d1, cadd_p(Cx<T>{pk[4 * mm], pk[4 * mm + 1]}, d1));
+            Cx<T> o2;
+            if (a.sigma == 0) {
+              o2 = cfma_p(bm1, dd2, cadd_p(Cx<T>{pk[4 * mm + 2], pk[4 * mm + 3]}, dd2));
+            } else {
+              const Cx<T> d2 = mul_i(dd2);
+              o2 = {(pk[4 * mm + 2] + d2.re) + bm1 * d2.re, (pk[4 * mm + 3] + d2.im) + bm1 * d2.im};
+            }
+            Q4<T> o = {o1.re, o1.im, o2.re, o2.im};
+            if (a.u_store && dbg_in(PG::upos_jm(j, m4), PG::U_N))
+              o = apply_u(u_z[PG::upos_jm(j, m4)], o);
+            o_out[mm] = o;
+          }
+        } else if constexpr (PG::SWAP) {
           // eigencomponent results of the pair meet in the staging buffer (the partner is
           // the neighbouring lane); thread c then finishes points m = 4c .. 4c + 3
           Cx<T>* stc = reinterpret_cast<Cx<T>*>(stage) + c;
@@ -890,6 +954,38 @@ __global__ void __launch_bounds__(1024, 1)
           }
         }
       }
+    }
+    if constexpr (TST) {
+      // ---- TST store: the staged line, then (after the barrier, which also frees the
+      // b - 1 / U zone) the next rows requested and the line's stores issued
+      if (!failed) {
+#pragma unroll
+        for (int mm = 0; mm < E / 2; ++mm) {
+          const int i = j + (4 * c + mm) * J;
+          if (dbg_in(i, (size_t)L)) reinterpret_cast<Q4<T>*>(psmem)[i] = o_out[mm];
+        }
+        fence_proxy_async_smem();  // the staging writes before the (async-proxy) stores
+      }
+      __syncthreads();
+      if (!failed && has_next) {
+        if (tid == 0) issue_bu((s + n_clusters) * CS + rank);
+        issued[1] += 1;
+      }
+      if (!failed && tid == 0) {
+        if (a.store_normal) {
+          if (dbg_in(gfirst + L - 1, (size_t)a.n_lines * L))
+            bulk_copy_s2g(a.out + gfirst, smem_u32(psmem), (uint32_t)(L * sizeof(Q4<T>)));
+        } else {
+          const int line = (int)(gfirst / L);
+#pragma unroll
+          for (int k = 0; k < L / TBOX; ++k)
+            if (dbg_in(line, (size_t)a.n_lines))
+              tma_store_2d(&tmap_out, smem_u32(psmem) + (uint32_t)(k * TBOX * sizeof(Q4<T>)),
+                           4 * line, k * TBOX);
+        }
+        bulk_commit();
+      }
+      continue;
     }
     if constexpr (CS > 1) {
       if (pend) {  // no forward FFT ran in this iteration (failure)
@@ -987,6 +1083,9 @@ __global__ void __launch_bounds__(1024, 1)
   if constexpr (CS > 1) {
     // the peer may still be reading this CTA's staged lines
     if (pend) cluster_wait();
+  }
+  if constexpr (TST) {
+    if (tid == 0) bulk_wait_all();  // the tile stays allocated until the stores are done
   }
   if (failed && tid == 0) {
     // at most one copy per mbarrier is outstanding: the last one requested
