@@ -199,6 +199,7 @@ static int fill_class(dirac_batch* b, Class& c, int K) {
       px.u_load = (!x->u_identity && !sl.started && k == 0) ? (const Q4<T>*)x->u_n : nullptr;
       px.u_store = nullptr;
       px.mult = (const Q4<T>*)x->mult_x;
+      px.mult_perm = (const Q4<T>*)x->mult_px;
       py.in = (const Q4<T>*)x->psiT;
       py.out = (Q4<T>*)x->psi;
       py.beta = (const T*)x->beta2T;
@@ -206,6 +207,7 @@ static int fill_class(dirac_batch* b, Class& c, int K) {
       py.u_store = x->u_identity ? nullptr
                                  : (const Q4<T>*)(k + 1 == sl.left ? x->u_t : x->u2_t);
       py.mult = (const Q4<T>*)x->mult_y;
+      py.mult_perm = (const Q4<T>*)x->mult_py;
       // failure-detection test hook (dirac_test_timeout_next_step): the first x pass of
       // the context in this tick waits for bytes that never arrive
       px.test_extra_tx = k == 0 ? x->test_timeout_next : 0u;
@@ -420,6 +422,8 @@ static dirac_status autotune_class(dirac_batch* b, Class& c, int reps, bool* cha
     py.beta = (const T*)x->beta2T;
     px.mult = (const Q4<T>*)x->mult_x;
     py.mult = (const Q4<T>*)x->mult_y;
+    px.mult_perm = (const Q4<T>*)x->mult_px;
+    py.mult_perm = (const Q4<T>*)x->mult_py;
     py.u_store = x->u_identity ? nullptr : (const Q4<T>*)x->u2_t;
   }
   InstPtrs<T>* d_tab = nullptr;

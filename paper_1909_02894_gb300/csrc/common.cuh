@@ -217,6 +217,15 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Position of frequency k (< 1024) in the step-multiplier table of 1024-point lines that
+// the 1024-point persistent pass reads: its digit-swap FFT leaves frequency
+// s + 8 l4 + 64 m + 512 v0 in element m of the thread with warp slice s and lane bits
+// l4 = lane >> 2, v0 = (lane >> 1) & 1, so the table is ordered (m, v0, s, l4) and the 16
+// entries a warp reads for one m are two runs of 8 consecutive entries.
+__host__ __device__ constexpr int perm1024(int k) {
+  return ((k >> 6) & 7) * 128 + ((k >> 9) & 1) * 64 + (k & 7) * 8 + ((k >> 3) & 7);
+}
+
 // ---- asynchronous stores from shared memory (bulk-group completion)
 // Tiled tensor store of one 2D box from shared memory (128-B aligned) to global memory,
 // at element coordinates (x, y) of the tensor map; x times the element size a multiple of

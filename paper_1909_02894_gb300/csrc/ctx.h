@@ -53,6 +53,9 @@ struct dirac_ctx {
   void** k_vptr = nullptr;          // device copy of the basis pointers
   double* k_partials = nullptr;     // inner-product partial sums
   double* k_coef = nullptr;         // combination coefficients (device)
+  // complex64 axes of 1024 points: the step tables (x at dt and dt/2, y) in the order of
+  // perm1024, for the 1024-point persistent pass
+  void *mult_px = nullptr, *mult_py = nullptr, *mult_pxh = nullptr;
   void *mult_xh = nullptr, *u2_n = nullptr;  // symmetric order: x multipliers at dt/2,
                                              // U^2 in the normal layout
   int* d_err = nullptr;       // device error flag written by bounded waits

@@ -134,6 +134,8 @@ static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
   const bool need_u2n = ctx->scheme != DIRAC_SCHEME_II;  // U^2 applied in the normal layout
   if (sym && !ctx->mult_xh)
     CK(dalloc(ctx, &ctx->mult_xh, ctx->nx * sizeof(Q4<T>)), "allocate tables");
+  if (sym && ctx->mult_px && !ctx->mult_pxh)
+    CK(dalloc(ctx, &ctx->mult_pxh, ctx->nx * sizeof(Q4<T>)), "allocate tables");
   if (need_u2n && !ctx->u_identity && !ctx->u2_n)
     CK(dalloc(ctx, &ctx->u2_n, npts(ctx) * sizeof(Q4<T>)), "allocate half-step");
   if (!ctx->u_identity) {
@@ -160,6 +162,14 @@ static dirac_status tables_for_dt(dirac_ctx* ctx, double dt) {
   if (sym) {
     CK(launch_step_mult<T>(ctx->nx, ctx->ax, 0.5 * dt, (Q4<T>*)ctx->mult_xh, st),
        "x multipliers (dt/2)");
+    ctx->launches += 1;
+  }
+  // the same tables in the 1024-point persistent pass's order
+  const void* perm_src[3] = {ctx->mult_x, ctx->mult_y, ctx->mult_xh};
+  void* perm_dst[3] = {ctx->mult_px, ctx->mult_py, ctx->mult_pxh};
+  for (int t = 0; t < 3; ++t) {
+    if (!perm_dst[t]) continue;
+    CK(launch_perm1024<T>((const Q4<T>*)perm_src[t], (Q4<T>*)perm_dst[t], st), "multiplier order");
     ctx->launches += 1;
   }
   ctx->dt_cached = dt;
@@ -194,9 +204,11 @@ template <typename T>
 static dirac_status step_symmetric(dirac_ctx* ctx, long n) {
   LinePassArgs<T> ax = pass_args<T>(ctx, 0), ay = pass_args<T>(ctx, 1);
   ax.mult = (const Q4<T>*)ctx->mult_xh;
+  ax.mult_perm = (const Q4<T>*)ctx->mult_pxh;
   ax.beta = (const T*)ctx->beta1;
   ax.beta_im = (const T*)ctx->beta1_im;
   ay.mult = (const Q4<T>*)ctx->mult_y;
+  ay.mult_perm = (const Q4<T>*)ctx->mult_py;
   ay.beta = (const T*)ctx->beta2T;
   ay.beta_im = (const T*)ctx->beta2T_im;
   ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
@@ -525,11 +537,13 @@ static dirac_status step_impl(dirac_ctx* ctx, long n, double dt) {
   ax.in = (const Q4<T>*)ctx->psi;
   ax.out = (Q4<T>*)ctx->psiT;
   ax.mult = (const Q4<T>*)ctx->mult_x;
+  ax.mult_perm = (const Q4<T>*)ctx->mult_px;
   ax.beta = (const T*)ctx->beta1;
   ax.beta_im = (const T*)ctx->beta1_im;
   ay.in = (const Q4<T>*)ctx->psiT;
   ay.out = (Q4<T>*)ctx->psi;
   ay.mult = (const Q4<T>*)ctx->mult_y;
+  ay.mult_perm = (const Q4<T>*)ctx->mult_py;
   ay.beta = (const T*)ctx->beta2T;
   ay.beta_im = (const T*)ctx->beta2T_im;
   ax.test_extra_tx = ay.test_extra_tx = ctx->test_timeout_next;
@@ -656,6 +670,10 @@ static dirac_status create_impl(dirac_ctx* ctx, const double* g_host[3]) {
     CK(dalloc(ctx, &ctx->tw_y_alt, ny * sizeof(Cx<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->mult_x, nx * sizeof(Q4<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->mult_y, ny * sizeof(Q4<T>)), "allocate tables");
+  if (sizeof(T) == 4 && nx == 1024)  // the 1024-point persistent pass's table order
+    CK(dalloc(ctx, &ctx->mult_px, nx * sizeof(Q4<T>)), "allocate tables");
+  if (sizeof(T) == 4 && ny == 1024)
+    CK(dalloc(ctx, &ctx->mult_py, ny * sizeof(Q4<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->dmult_x, nx * sizeof(Q4<T>)), "allocate tables");
   CK(dalloc(ctx, &ctx->dmult_y, ny * sizeof(Q4<T>)), "allocate tables");
   CK(dalloc(ctx, (void**)&ctx->staging, 2 * n * 2 * sizeof(double)), "allocate staging");
@@ -773,6 +791,7 @@ static dirac_status tune_pass(dirac_ctx* ctx, int axis, int reps, int* best, flo
   a.in = (const Q4<T>*)ctx->psi;  // any data of the pass's shape: the time does not depend on it
   a.out = (Q4<T>*)ctx->scratch1;
   a.mult = (const Q4<T>*)(axis == 0 ? ctx->mult_x : ctx->mult_y);
+  a.mult_perm = (const Q4<T>*)(axis == 0 ? ctx->mult_px : ctx->mult_py);
   a.beta = (const T*)(axis == 0 ? ctx->beta1 : ctx->beta2T);
   a.u_store = (axis == 1 && !ctx->u_identity) ? (const Q4<T>*)ctx->u2_t : nullptr;
   const int L = a.L;

@@ -73,6 +73,8 @@ cudaError_t launch_twiddles(int n, int e, Cx<T>* tw, cudaStream_t st);
 template <typename T>
 cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream_t st);
 template <typename T>
+cudaError_t launch_perm1024(const Q4<T>* src, Q4<T>* dst, cudaStream_t st);
+template <typename T>
 cudaError_t launch_deriv_mult(int n, double a, Q4<T>* mult, cudaStream_t st);
 
 // Half step with static potentials: general complex U and U^2 per point (normal layout,

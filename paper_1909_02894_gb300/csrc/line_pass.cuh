@@ -44,6 +44,7 @@ struct InstPtrs {
   const Q4<T>* u_load;
   const Q4<T>* u_store;
   const Q4<T>* mult;
+  const Q4<T>* mult_perm;  // see LinePassArgs
   unsigned test_extra_tx;  // test hook of this instance (see LinePassArgs); 0 normally
 };
 
@@ -58,6 +59,8 @@ struct LinePassArgs {
   const Cx<T>* tw_alt;  // the same for the alternative radix schedule (or nullptr)
   const Q4<T>* mult;    // per k index q: step ((cos - 1) hi, lo, sin hi, lo) / (2L);
                         // derivative (0, 0, xi hi, xi lo) / L
+  const Q4<T>* mult_perm;  // 1024-point lines: the step table with entry q at perm1024(q),
+                           // read by the 1024-point persistent pass; or nullptr
   const T* beta;        // b - 1 per input point, or nullptr (b = 1)
   const T* beta_im;     // imaginary part of b - 1 (complex stretching), or nullptr
   const Q4<T>* u_load;  // U applied to psi when it is read, or nullptr
@@ -90,6 +93,7 @@ __device__ __forceinline__ void bind_instance(LinePassArgs<T>& a, int k) {
   a.u_load = p.u_load;
   a.u_store = p.u_store;
   a.mult = p.mult;
+  a.mult_perm = p.mult_perm;
   a.test_extra_tx = p.test_extra_tx;
 }
 

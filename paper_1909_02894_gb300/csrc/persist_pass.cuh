@@ -808,13 +808,20 @@ __global__ void __launch_bounds__(1024, 1)
       }
       // frequency of element m: j + m J, or for the 1024-point FFT
       // slice + 8 (lane >> 2) + 64 m + 512 ((lane >> 1) & 1)
-      const int kb = PG::SWAP1K ? (warp >> 2) + 8 * (lane >> 2) + 512 * ((lane >> 1) & 1) : j;
-      constexpr int KS = PG::SWAP1K ? 64 : J;
+      // (the 1024-point FFT reads the permuted table when there is one: the natural one puts
+      // a warp's 16 entries 128 B apart, in the same banks of L1)
+      const Q4<T>* mb = a.mult + j;
+      int ks = J;
+      if constexpr (PG::SWAP1K) {
+        const int l4 = lane >> 2, v0 = (lane >> 1) & 1, sl = warp >> 2;
+        mb = a.mult_perm ? a.mult_perm + (v0 * 64 + sl * 8 + l4) : a.mult + (sl + 8 * l4 + 512 * v0);
+        ks = a.mult_perm ? 128 : 64;
+      }
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         if constexpr (!PG::SWAP)
           if ((m & 3) == 0) asm volatile("" ::: "memory");  // at most 4 loads in flight
-        const Q4<T> q = ldg_q4(a.mult + kb + m * KS);
+        const Q4<T> q = ldg_q4(mb + m * ks);
         const T vr = v[m].re, vi = v[m].im;
         const T sh = -sg * q.z, sl = -sg * q.w;
         v[m] = {q.x * vr + ((q.y * vr - sl * vi) - sh * vi),

@@ -349,6 +349,30 @@ cudaError_t launch_step_mult(int n, double a, double dt, Q4<T>* mult, cudaStream
   return cudaGetLastError();
 }
 
+constexpr bool perm1024_is_a_permutation() {
+  bool seen[1024] = {};
+  for (int k = 0; k < 1024; ++k) {
+    const int p = perm1024(k);
+    if (p < 0 || p >= 1024 || seen[p]) return false;
+    seen[p] = true;
+  }
+  return true;
+}
+static_assert(perm1024_is_a_permutation(), "perm1024 must map 0..1023 onto itself");
+
+// dst[perm1024(q)] = src[q] for the 1024 entries of a 1024-point step table
+template <typename T>
+__global__ void k_perm1024(const Q4<T>* __restrict__ src, Q4<T>* __restrict__ dst) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < 1024) dst[perm1024(q)] = src[q];
+}
+
+template <typename T>
+cudaError_t launch_perm1024(const Q4<T>* src, Q4<T>* dst, cudaStream_t st) {
+  k_perm1024<T><<<nblocks(1024), TPB, 0, st>>>(src, dst);
+  return cudaGetLastError();
+}
+
 template <typename T>
 __global__ void k_deriv_mult(int n, double a, Q4<T>* mult) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
@@ -402,6 +426,7 @@ cudaError_t launch_transpose(const Q4<T>* in, Q4<T>* out, int rows, int cols, cu
       cudaStream_t);                                                                         \
   template cudaError_t launch_twiddles<T>(int, int, Cx<T>*, cudaStream_t);                    \
   template cudaError_t launch_step_mult<T>(int, double, double, Q4<T>*, cudaStream_t);        \
+  template cudaError_t launch_perm1024<T>(const Q4<T>*, Q4<T>*, cudaStream_t);                \
   template cudaError_t launch_deriv_mult<T>(int, double, Q4<T>*, cudaStream_t);               \
   template cudaError_t launch_transpose<T>(const Q4<T>*, Q4<T>*, int, int, cudaStream_t);
 INST(float)
