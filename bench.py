@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -93,10 +94,19 @@ def fft_flops_per_point_step(nx, ny):
     return 20.0 * (np.log2(nx) + np.log2(ny)) + 76.0
 
 
+KERNEL_SOURCES = ("line_pass.cuh", "persist_pass.cuh", "launch_impl.cuh", "common.cuh")
+
+
 def kernel_hash():
+    """Hash of the line-pass kernel sources with comments and spacing removed: the committed
+    ncu counters (profiles/*traffic.txt) stay valid across comment edits, and any change of
+    code voids them."""
     h = hashlib.sha256()
-    for f in ("line_pass.cuh", "persist_pass.cuh", "launch_impl.cuh", "common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_1909_02894_gb300", "csrc", f), "rb").read())
+    for f in KERNEL_SOURCES:
+        src = open(os.path.join(ROOT, "paper_1909_02894_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

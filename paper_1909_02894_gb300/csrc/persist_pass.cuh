@@ -41,12 +41,14 @@ struct PGeo {
   static constexpr int THREADS = 1024;
   static constexpr int TPL = 2 * L / E;
   static constexpr int LPI = THREADS / TPL;  // lines per group
-  // CTAs per cluster: 2 for 4096-point lines, whose output then leaves in 32-byte
-  // (one DRAM sector) segments of 2 lines. Clusters of 2 keep every SM busy (76 x 2 CTAs
-  // resident on 152 SMs; clusters of 4 fit only 36 x 4) and measured faster than both
-  // clusters of 4 (64-B segments) and no cluster (16-B segments). Shorter lines write
-  // LPI-line segments without a cluster (the cluster barriers cost more than they saved at
-  // 2048 points).
+  // CTAs per cluster: 2 for 4096-point lines (adjacent lines run together). Batched
+  // launches gather their output into 32-byte (one DRAM sector) segments of the 2 lines;
+  // single-instance launches write each CTA's line with tensor stores, and the two halves
+  // of each sector arrive at about the same time. Clusters of 2 keep every SM busy (76 x 2
+  // CTAs resident on 152 SMs; clusters of 4 fit only 36 x 4) and measured faster than both
+  // clusters of 4 (64-B segments) and no cluster (16-B register stores). Shorter lines
+  // write LPI-line segments without a cluster (the cluster barriers cost more than they
+  // saved at 2048 points).
   static constexpr int CS = L == 4096 ? 2 : 1;
   static constexpr int GL = LPI * CS;               // lines per output segment
   using G = Geo<T, L, LPI, E>;               // FFT buffer plan (padded, conflict-free)
@@ -650,10 +652,11 @@ __global__ void __launch_bounds__(1024, 1)
   uint32_t issued[2] = {TICK ? 0u : first_issue, first_issue};
   uint32_t done[2] = {0u, 0u};
   int it = 0;
-  // clusters: the barrier after the transposed store is split; its arrive ends an
-  // iteration and its wait comes just before the next write into the staging area (the
-  // forward FFT's shared-memory exchange), so the load and the first FFT passes overlap
-  // the peer's gather. pend: an arrive awaits its wait (uniform across the cluster)
+  // clusters with a gather (batched launches): the barrier after the transposed store is
+  // split; its arrive ends an iteration and its wait comes just before the next write into
+  // the staging area (the forward FFT's shared-memory exchange), so the load and the first
+  // FFT passes overlap the peer's gather. pend: an arrive awaits its wait (uniform across
+  // the cluster; never set on the TST path)
   bool pend = false;
   for (int s = cluster_id;; s += n_clusters, ++it) {
     // TICK: this iteration's item, the next one and the one after (thread 0 decodes it)

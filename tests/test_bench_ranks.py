@@ -76,3 +76,23 @@ def test_traffic_summaries_are_keyed_as_the_bench_looks_them_up(tmp_path, monkey
     assert bench.ncu_traffic(name, "c64") == 123.0
     assert bench.ncu_traffic(name, "c128") is None
     assert bench.ncu_traffic("large-4096", "c64") is None
+
+
+def test_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    """The committed ncu counters are keyed by a hash of the kernel code: a comment edit
+    keeps it, any code edit changes it."""
+    import shutil
+
+    src = os.path.join(bench.ROOT, "paper_1909_02894_gb300", "csrc")
+    dst = tmp_path / "paper_1909_02894_gb300" / "csrc"
+    dst.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(src, f), dst / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_hash()
+    p = dst / "common.cuh"
+    text = p.read_text()
+    p.write_text(text + "\n// a comment\n/* another\n   comment */\n")
+    assert bench.kernel_hash() == h0
+    p.write_text(text + "\nstatic const int dgb_unused_for_hash_test = 1;\n")
+    assert bench.kernel_hash() != h0
