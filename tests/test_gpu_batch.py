@@ -156,3 +156,32 @@ def test_batch_matches_oracle_and_admits_late_arrivals():
         D.dirac_batch_destroy(batch)
         for s in (s1, s2, s3):
             s.close()
+
+
+def test_batched_4096_point_lines_equal_the_alone_run():
+    """A 4096^2 instance in a batch (clusters of two CTAs gather the output through
+    distributed shared memory and store it from registers) gives, bit for bit, the result
+    of the same instance stepped alone (each CTA's line written by tensor stores), beside a
+    small instance of another class."""
+    rng = np.random.default_rng(17)
+    ws = [W.batched_instance(4096, rng, steps=6), W.batched_instance(256, rng, steps=9)]
+    ref = [alone(w, D.DIRAC_C64) for w in ws]
+    batch = D.dirac_batch_create(64 << 30, D.DIRAC_C64, steps_per_tick=4)
+    sims, slots = [], []
+    try:
+        for w in ws:
+            s = D.Simulation(w, precision=D.DIRAC_C64)
+            s.set_state(w.psi0)
+            sims.append(s)
+            slots.append(D.dirac_batch_submit(batch, s.ctx, w.steps, w.dt))
+        while D.dirac_batch_active(batch):
+            D.dirac_batch_run(batch, 1)
+        D.dirac_batch_synchronize(batch)
+        for w, s, sl, r in zip(ws, sims, slots, ref):
+            D.dirac_batch_release(batch, sl)
+            got = s.get_state()
+            assert np.array_equal(got, r), (w.name, W.rel_l2(got, r))
+    finally:
+        D.dirac_batch_destroy(batch)
+        for s in sims:
+            s.close()
