@@ -594,7 +594,8 @@ def serve_record(args, stream, rate, window, check=True, plain_rates=None):
     if check and reqs and not any(r.check for r in reqs):
         reqs[0].check = True
     work = sum(r.nx * r.ny * r.steps for r in reqs)
-    srv = S.Server(budget, steps_per_tick=args.tick, stream=stream.cuda_stream)
+    srv = S.Server(budget, steps_per_tick=args.tick, stream=stream.cuda_stream,
+                   policy=args.serve_policy, max_active_points=args.serve_cap_points)
     try:
         for r in reqs:
             srv.submit(r)
@@ -608,7 +609,9 @@ def serve_record(args, stream, rate, window, check=True, plain_rates=None):
     summ.update({"rate_per_s": rate, "window_s": window, "throughput": work / elapsed,
                  "unit": UNIT, "elapsed_s": elapsed, "max_active": srv.max_active,
                  "admitted_while_busy": srv.admitted_while_busy, "ticks": srv.ticks,
-                 "budget_bytes": budget, "clocks": clk.summary(), "dtype": "f32"})
+                 "budget_bytes": budget, "clocks": clk.summary(), "dtype": "f32",
+                 "policy": args.serve_policy,
+                 "max_active_points": args.serve_cap_points if args.serve_policy == "sjf" else None})
     if plain_rates:
         # the same requests, each alone on the plain complex128 path
         t_plain = sum(r.nx * r.ny * r.steps / plain_rates[r.nx] for r in reqs
@@ -683,6 +686,11 @@ def main():
                          "--profile-from-start off)")
     ap.add_argument("--check-steps", type=int, default=5,
                     help="steps of the default line's rel-L2 check against the oracle")
+    ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
+                    help="admission order of the serving loop: arrival order, or the least "
+                         "work first under a cap on the active grid points")
+    ap.add_argument("--serve-cap-points", type=int, default=16 << 20,
+                    help="sjf: most grid points of the requests running at once")
     ap.add_argument("--sustainable-rate", type=float, default=4.0)
     ap.add_argument("--sustainable-seconds", type=float, default=20.0)
     ap.add_argument("--scheme", default="printed",

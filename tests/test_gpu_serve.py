@@ -81,3 +81,45 @@ def test_served_large_grids_equal_alone_runs():
     for res in results:
         req = by_id[res.rid]
         assert np.array_equal(res.state, alone(req.make(), req.steps)), res.rid
+
+
+def test_shortest_job_first_admission_keeps_results_and_orders_by_work():
+    """The sjf policy admits the arrived request with the least work first and keeps the
+    active points under the cap; every result still equals the alone run bit for bit."""
+    D.build()
+    reqs = S.graphene_requests(rate=400.0, duration=0.05, seed=33, sizes=(64, 128, 256),
+                               steps_range=(20, 120), check_fraction=0.0)
+    assert len(reqs) >= 8
+    for r in reqs:  # everything has arrived at the start
+        r.arrival = 0.0
+    cap = 256 * 256 + 128 * 128
+    srv = S.Server(1 << 34, steps_per_tick=8, keep_states=True, policy="sjf",
+                   max_active_points=cap)
+    started = []
+    orig = srv._start
+
+    def spy(req, need):
+        started.append((req.nx * req.ny * req.steps, req.rid, srv.active_points))
+        orig(req, need)
+
+    srv._start = spy
+    try:
+        for r in reqs:
+            srv.submit(r)
+        results = srv.run(deadline=300.0)
+    finally:
+        srv.close()
+    assert len(results) == len(reqs)
+    # the first admissions come in order of work, and the cap is respected whenever
+    # something else was running
+    first = [w for w, _, _ in started[:3]]
+    assert first == sorted(first)
+    by_id = {r.rid: r for r in reqs}
+    for w, rid, before in started:
+        if before:
+            assert before + by_id[rid].nx * by_id[rid].ny <= cap
+    for res in results:
+        req = by_id[res.rid]
+        assert np.array_equal(res.state, alone(req.make(), req.steps)), res.rid
+    with pytest.raises(ValueError):
+        S.Server(1 << 30, policy="lifo")
