@@ -34,7 +34,7 @@ from . import workloads as W
 @dataclass(order=True)
 class Request:
     arrival: float
-    rid: int = field(compare=False)
+    rid: int  # orders requests that arrive at the same time
     make: Callable[[], "W.Workload"] = field(compare=False)
     nx: int = field(compare=False)
     ny: int = field(compare=False)
