@@ -96,3 +96,22 @@ def test_kernel_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
     assert bench.kernel_hash() == h0
     p.write_text(text + "\nstatic const int dgb_unused_for_hash_test = 1;\n")
     assert bench.kernel_hash() != h0
+
+
+def test_clock_summary_reports_the_median_and_every_active_reason():
+    """The clock record of a bench line: median SM clock under load, the highest max clock,
+    and each throttle reason seen Active in any sample (nvidia-smi csv, noheader, nounits)."""
+    c = bench.Clocks(0)
+    c.out = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1500, 2070, 1400.0, 0x0000000000000040, Not Active, Active, Not Active, Active",
+        "garbage line",
+    ])
+    s = c.summary()
+    assert s["samples"] == 4
+    assert s["sm_mhz"] == 2025.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    c.out = ""
+    assert c.summary()["reasons"] == ["unsampled"]
