@@ -1,6 +1,6 @@
-"""The reference arm of bench.py (the FP64 oracle timed on the host cores) on the CPU: one
+"""The FP64 oracle timed on the host cores, on the CPU: the reference arm of bench.py (one
 JSON line with the keys the benchmark contract names, and the same metric and unit as the
-GPU arm."""
+GPU arm) and the cpu_baseline record's sample calibration."""
 import json
 import os
 import subprocess
@@ -43,3 +43,20 @@ def test_reference_arm_on_a_rank_other_than_zero_prints_nothing():
                           "reference", "--steps", "1", "--warmup", "0"],
                          capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert out.returncode == 0 and out.stdout.strip() == ""
+
+
+def test_cpu_baseline_lengthens_the_sample_on_a_tiny_grid():
+    """On a grid so small that a 2-step run takes microseconds, the oracle baseline keeps
+    lengthening its runs until the timed difference is long enough: the rate stays finite
+    and plausible instead of a division by timer noise, and the sample says how many steps
+    it took."""
+    import bench
+    from paper_1909_02894_gb300 import workloads as W
+
+    w = W.plain_128(n=16, steps=1)
+    rec, state = bench.cpu_baseline(w, check_steps=2)
+    assert state.shape == (2, 16, 16)
+    assert 0 < rec["value"] < 1e11
+    steps = int(rec["sample"].split("difference of ")[1].split("-step")[0])
+    assert steps > 2
+    assert 0 < rec["single_thread"]["value"] < 1e11
